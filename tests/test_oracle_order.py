@@ -1,0 +1,142 @@
+"""Pins of the oracle's order score (Eq. 6) and greedy best graph (Algorithm 1)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _table(name="n6_k2_m100", seed_offset=0, **kw):
+    data, arity, k, R, net = synth.workload(name, seed_offset)
+    return oracle.build_table(data, arity, k, R=R, **kw), k, data, arity
+
+
+def _node_masks(n, k):
+    """(n, S) node-id bitmask of every (node, rank) parent set."""
+    S = oracle.num_sets(n - 1, k)
+    M = np.zeros((n, S), np.int64)
+    for i in range(n):
+        for r in range(S):
+            for p in oracle.parent_set(n, k, i, r):
+                M[i, r] |= 1 << p
+    return M
+
+
+def _max_over_dags(T, masks):
+    """Exhaustive max of the Eq. (9) graph score over every DAG whose nodes draw their
+    parent sets from the table (in-degree <= k): every combination of per-node parent
+    sets, keeping the acyclic ones (repeatedly removing nodes without remaining
+    parents).  Vectorised over the last n-2 nodes."""
+    n, S = T.shape
+    best = -np.inf
+    grids = np.meshgrid(*[np.arange(S)] * (n - 2), indexing="ij")
+    rest = [g.ravel() for g in grids]
+    rest_score = sum(T[i + 2][rest[i]] for i in range(n - 2))
+    rest_mask = [masks[i + 2][rest[i]] for i in range(n - 2)]
+    for r0 in range(S):
+        for r1 in range(S):
+            P = [np.full(rest[0].shape, masks[0][r0]), np.full(rest[0].shape, masks[1][r1])] + rest_mask
+            removed = np.zeros(rest[0].shape, np.int64)
+            for _ in range(n):
+                for i in range(n):
+                    can = (P[i] & ~removed) == 0
+                    removed |= np.where(can, np.int64(1) << i, 0)
+            ok = removed == (1 << n) - 1
+            if ok.any():
+                best = max(best, float((T[0][r0] + T[1][r1] + rest_score)[ok].max()))
+    return best
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("seed_offset,kind", [(0, 0), (1, 0), (2, 1)])
+def test_best_order_equals_best_dag_n6(seed_offset, kind):
+    """Sec. III.B: with the max-based order score the globally best graph is
+    consistent with the globally best order, so the max over all 720 orders equals the
+    max over all DAGs with in-degree <= k."""
+    T, k, _, _ = _table(seed_offset=seed_offset, kind=kind, ess=2.0)
+    n = T.shape[0]
+    best_order = max(oracle.order_score(T, k, np.array(o, np.uint8))[0]
+                     for o in itertools.permutations(range(n)))
+    best_dag = _max_over_dags(T, _node_masks(n, k))
+    assert best_order == pytest.approx(best_dag, rel=1e-14, abs=1e-12)
+
+
+def test_best_order_equals_best_dag_n5_k3():
+    data, arity, _, _, _ = synth.workload("n6_k2_m100", 3)
+    data = data[:, :5].copy()
+    arity = arity[:5].copy()
+    k = 3
+    R = np.full((5, 5), 0.5)
+    R[1, 0] = 0.9
+    R[3, 2] = 0.1
+    T = oracle.build_table(data, arity, k, R=R)
+    best_order = max(oracle.order_score(T, k, np.array(o, np.uint8))[0]
+                     for o in itertools.permutations(range(5)))
+    assert best_order == pytest.approx(_max_over_dags(T, _node_masks(5, k)), rel=1e-14)
+
+
+def test_order_score_decomposes_over_a_full_scan():
+    """The per-node maximum of Eq. (6) taken over every table entry whose parent set
+    lies in the node's predecessors (a scan over all ranks, the opposite enumeration to
+    the oracle's subset walk), ties to the lowest rank; the order score is their sum."""
+    T, k, _, _ = _table("n20_k4_m1000")
+    n, S = T.shape
+    masks = _node_masks(n, k)
+    orders = synth.random_orders(n, 6, 77)
+    for o in orders:
+        s, br = oracle.order_score(T, k, o)
+        pos = np.empty(n, np.int64)
+        pos[o] = np.arange(n)
+        ref_total = 0.0
+        for i in range(n):
+            pred = 0
+            for v in range(n):
+                if pos[v] < pos[i]:
+                    pred |= 1 << v
+            ok = (masks[i] & ~pred) == 0
+            vals = np.where(ok, T[i], -np.inf)
+            r = int(np.argmax(vals))           # first (lowest-rank) maximum
+            assert br[i] == r
+            ref_total += T[i, r]
+        assert s == ref_total
+
+
+def test_greedy_dag_invariants():
+    T, k, _, _ = _table("n20_k4_m1000")
+    n = T.shape[0]
+    for o in synth.random_orders(n, 10, 5):
+        s, br = oracle.order_score(T, k, o)
+        adj = oracle.greedy_dag(n, k, br)
+        pos = np.empty(n, np.int64)
+        pos[o] = np.arange(n)
+        # every edge m -> i goes from an earlier to a later position (hence acyclic)
+        for i in range(n):
+            for m in range(n):
+                if adj[i, m]:
+                    assert pos[m] < pos[i]
+        assert adj.sum(axis=1).max() <= k
+        # its Eq. (9) score recomputed from the table is the order score, bit for bit
+        assert oracle.graph_score(T, k, br) == s
+        # the first node can only take the empty set; the last node takes its
+        # unconstrained best entry
+        assert br[o[0]] == 0
+        last = o[-1]
+        assert br[last] == int(np.argmax(T[last]))
+
+
+def test_ties_go_to_lowest_rank():
+    n, k = 5, 2
+    S = oracle.num_sets(n - 1, k)
+    T = np.zeros((n, S))                   # every entry ties
+    for o in synth.random_orders(n, 5, 3):
+        s, br = oracle.order_score(T, k, o)
+        assert (br == 0).all() and s == 0.0
+    T2 = np.full((n, S), -5.0)
+    T2[:, 7] = -1.0                        # a single best entry in every row
+    T2[:, 9] = -1.0                        # and a tie above it
+    o = np.arange(n, dtype=np.uint8)
+    _, br = oracle.order_score(T2, k, o[::-1].copy())
+    last = n - 1 - 0
+    assert br[0] == 7                      # node 0 is last in the reversed order
