@@ -1,0 +1,211 @@
+/*
+ * bn.h -- C ABI of the GB300 order-space Bayesian-network scorer.
+ *
+ * The library implements the data-parallel hot path of the order-space MCMC learner of
+ * Wang, Zhang, Qian and Yuan, "A Novel Learning Algorithm for Bayesian Network and Its
+ * Efficient Implementation on GPU" (arXiv:1210.5128):
+ *   - the local-score table of every (node, parent set of size <= k)     Sec. III.A, Eq. (3)-(4)
+ *     with the pairwise prior folded in                                  Sec. IV, Eq. (9)-(10)
+ *   - the order score: per node the best parent set drawn from its
+ *     predecessors, summed over nodes                                    Sec. III.B, Eq. (6)
+ *   - the Metropolis-Hastings swap sampler and best-graph tracking       Sec. III.C, Algorithm 1
+ * All compute runs in CUDA kernels for sm_103a; every entry point is synchronous with
+ * respect to the stream it is given (it returns after its work on that stream is done).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: BN_OK (0) or a negative BN_E* code; bn_last_error() then holds a
+ *     one-line message for the calling thread.  No entry point aborts the process.
+ *   - `mem` says where the caller's array arguments live: BN_MEM_HOST (ordinary or
+ *     pinned host memory) or BN_MEM_DEVICE (device memory of the current device, e.g. a
+ *     torch tensor's data_ptr()).  All array arguments of one call use the same `mem`.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Nodes are numbered 0..n-1, 2 <= n <= 64.  Parent sets of node i live in its
+ *     "candidate space": slot c (0 <= c < n-1) stands for node c + (c >= i).
+ *   - A parent set's rank orders all subsets of size <= k of the n-1 candidate slots:
+ *     sizes ascending (the empty set is rank 0), and within one size the
+ *     combinatorial number system, rank {a_1 < ... < a_j} = sum_t C(a_t, t)
+ *     (Sec. V.B asks for such a regular, invertible indexing; this is the choice made).
+ *     S(n-1, k) = sum_{j<=k} C(n-1, j) sets per node (Sec. III.B).
+ *   - Ties between equal local scores always go to the lowest rank.
+ *   - Orders are arrays of n node ids, position -> node.
+ */
+#ifndef BN_H
+#define BN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BN_OK            0
+#define BN_EINVAL       -1   /* invalid argument (sizes, values, NaN, NULL) */
+#define BN_ENOMEM       -2   /* a device or host allocation failed */
+#define BN_ECUDA        -3   /* a CUDA runtime call failed (message has the CUDA error) */
+#define BN_ETIMEOUT     -4   /* a bounded device-side wait expired; the kernel gave up */
+#define BN_EUNSUPPORTED -5   /* valid request outside this build's limits */
+
+#define BN_MEM_HOST   0
+#define BN_MEM_DEVICE 1
+
+/* ---------------------------------------------------------------------------------- */
+/* Local-score table                                                                   */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct bn_table bn_table;   /* opaque, device-resident, owned by the library */
+
+typedef struct {
+    int    score_kind;   /* 0 = K2 (alpha_cx = 1, alpha_c = r_i); 1 = BDeu(ess)          */
+    double ess;          /* BDeu equivalent sample size (> 0); ignored for K2           */
+    double log10_gamma;  /* log10 of the structure penalty gamma of Eq. (3); 0 = none   */
+} bn_score_params;
+
+/* Build the local-score table of Eq. (4) plus the prior of Eq. (9) for every node and
+ * every parent set of size <= k (the preprocessing step of Sec. III.A):
+ *   entry(i, pi) = ls(i, pi) + sum_{m in pi} PPF(i, m),  PPF = 100 (R[i][m] - 0.5)^3.
+ *   data   m x n uint8, row-major, data[r*n + i] < arity[i]   (m >= 0; complete data)
+ *   arity  n uint8 in [2, 4]
+ *   k      0 <= k <= n-1, and the per-node set count and q*r count table must fit
+ *   R      n x n float64 in [0, 1], R[i*n + m] = prior belief in the edge m -> i
+ *          (Sec. IV: 0.5 = no bias); NULL = 0.5 everywhere; the diagonal is ignored
+ *   params NULL = K2 with gamma = 1
+ * Scores are FP64.  Counts are exact integers; the lgamma terms of one entry are summed
+ * exactly (128-bit fixed point) before one rounding to FP64.
+ * Errors: BN_EINVAL for n, k, arity, data or R out of range (R NaN included);
+ * BN_EUNSUPPORTED if S(n-1,k) >= 2^31 or a count table needs more than 4096 cells;
+ * BN_ENOMEM; BN_ECUDA.  On error *out is NULL. */
+int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                    const double* R, const bn_score_params* params, int mem,
+                    void* stream, bn_table** out);
+
+/* Wrap an existing table of scores (n x S(n-1,k) float64, node-major, rank order; the
+ * layout bn_table_scores returns).  Used to score orders against an externally built
+ * table.  Errors: BN_EINVAL (NaN or +inf scores, sizes), BN_ENOMEM, BN_ECUDA. */
+int bn_table_from_scores(const double* scores, int n, int k, int mem, void* stream,
+                         bn_table** out);
+
+/* n, k, S(n-1,k) and the device bytes the table holds (any output may be NULL). */
+int bn_table_info(const bn_table* t, int* n, int* k, int64_t* sets_per_node,
+                  int64_t* device_bytes);
+
+/* Copy out the S(n-1,k) FP64 scores of one node (rank order), or of all nodes when
+ * node == -1 (n x S, node-major). */
+int bn_table_scores(const bn_table* t, int node, double* out, int mem, void* stream);
+
+void bn_table_free(bn_table* t);
+
+/* ---------------------------------------------------------------------------------- */
+/* Order scoring                                                                       */
+/* ---------------------------------------------------------------------------------- */
+
+/* Score B orders (Eq. (6), the scoring loop of Algorithm 1):
+ *   orders      B x n uint8, each row a permutation of 0..n-1 (position -> node)
+ *   best_rank   B x n uint32 out: best_rank[b*n + i] = rank of node i's best parent
+ *               set among those drawn from its predecessors in order b (lowest rank
+ *               among equal scores); its greedy best graph (Sec. III.B)
+ *   order_score B float64 out: sum over nodes, ascending node id, of those entries
+ * Either output may be NULL.  B = 0 is a no-op.  Scratch is allocated per call.
+ * Errors: BN_EINVAL (not a permutation, B < 0), BN_ENOMEM, BN_ECUDA. */
+int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
+                    double* order_score, int mem, void* stream);
+
+/* Candidate-space mask of a rank and back (host-side helpers, no GPU needed).
+ * mask bit c = candidate slot c.  Errors: BN_EINVAL if rank >= S(N,k) or the mask has
+ * more than k bits or bits at or above N. */
+int bn_unrank(int N, int k, int64_t rank, uint64_t* mask);
+int bn_rank(int N, int k, uint64_t mask, int64_t* rank);
+
+/* ---------------------------------------------------------------------------------- */
+/* Metropolis-Hastings swap sampler                                                    */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct bn_chains bn_chains;  /* opaque, device-resident chain state */
+
+/* Random numbers (one definition, key = {seed, 0}, Philox4x64-10):
+ *   initial order of chain c: Fisher-Yates from the identity; for i = n-1..1 swap
+ *     positions i and floor(x*(i+1)/2^64), x the next word of the blocks
+ *     Philox(ctr = {j, c, 1, 0}), j = 0, 1, ...
+ *   step t of chain c: x = Philox(ctr = {t, c, 0, 0}); the swapped positions are pair
+ *     floor(x0 * P / 2^64) of the P = n(n-1)/2 pairs (a < b) in lexicographic order;
+ *     u = ((x1 >> 12) + 0.5) 2^-52. */
+typedef struct {
+    int      chains;      /* independent chains, 1 .. 65536                             */
+    int64_t  burn_in;     /* steps before edge counting starts                          */
+    uint64_t seed;
+    int      literal_log; /* 0: accept iff ln u < ln10 (s' - s)  (exact MH for the target
+                             proportional to 10^score); 1: ln u < s' - s as printed     */
+    int      record_every;/* >0: record every record_every-th post-burn-in state's edge
+                             indicators for the ESS estimate; 0: off                     */
+    int      record_cap;  /* max recorded states per chain (ESS series length)          */
+    int      trace;       /* 1: keep per-step score and accept flag (chains x steps cap) */
+    int64_t  trace_cap;   /* steps of trace kept per chain                              */
+} bn_mcmc_params;
+
+/* Create chains over a table.  init_orders: chains x n (NULL = Philox initial orders,
+ * see above).  The table must outlive the chains. */
+int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, const uint8_t* init_orders,
+                     int mem, void* stream, bn_chains** out);
+
+/* Advance every chain by `steps` MH steps (Algorithm 1 iterations).  Each step
+ * proposes a swap, re-scores only the nodes between the swapped positions (the
+ * others keep their predecessor sets, so their best parent sets are unchanged),
+ * applies the MH test, updates the best graph (strictly better replaces; candidates are
+ * the initial and the accepted orders) and, after burn-in, the edge counts of the
+ * current state's greedy DAG.  Steps are replayed from a captured CUDA graph.
+ * Errors: BN_ETIMEOUT, BN_ECUDA. */
+int bn_chains_step(bn_chains* c, int64_t steps, void* stream);
+
+/* bn_chains_step without the graph: the step's kernels are launched one by one on
+ * `stream` and every scan launch is bracketed by a pair of CUDA events; *scan_ms
+ * receives the summed device time of those launches and *scan_launches their number
+ * (either may be NULL).  Results are identical to bn_chains_step. */
+int bn_chains_step_profiled(bn_chains* c, int64_t steps, void* stream, double* scan_ms,
+                            int64_t* scan_launches);
+
+#define BN_OUT_ORDERS       1  /* chains x n uint8    current orders                     */
+#define BN_OUT_SCORES       2  /* chains float64      current order scores               */
+#define BN_OUT_RANKS        3  /* chains x n uint32   current best parent-set ranks      */
+#define BN_OUT_BEST_ORDERS  4  /* chains x n uint8                                       */
+#define BN_OUT_BEST_SCORES  5  /* chains float64                                         */
+#define BN_OUT_BEST_RANKS   6  /* chains x n uint32                                      */
+#define BN_OUT_EDGE_COUNTS  7  /* chains x n x n uint32, [c][i][m]: steps with m -> i    */
+#define BN_OUT_ACCEPTS      8  /* chains int64                                           */
+#define BN_OUT_TRACE_SCORE  9  /* chains x trace_cap float64 (score after each step)     */
+#define BN_OUT_TRACE_ACCEPT 10 /* chains x trace_cap uint8                               */
+#define BN_OUT_STEPS        11 /* 1 int64: steps taken so far                            */
+#define BN_OUT_ESS          12 /* n x n float64: Geyer initial-monotone-sequence ESS of
+                                  each edge indicator series, summed over the chains in
+                                  which it is not constant (NaN where all are constant) */
+#define BN_OUT_RECORD       13 /* chains x n x n x ceil(record_cap/64) uint64: recorded
+                                  edge-indicator series, bit r of [c][i][m] = edge m -> i
+                                  in chain c's r-th recorded state                       */
+#define BN_OUT_RECORD_LEN   14 /* 1 int64: states recorded so far per chain              */
+int bn_chains_read(const bn_chains* c, int what, void* out, int mem, void* stream);
+
+void bn_chains_free(bn_chains* c);
+
+/* One-shot run (Algorithm 1): chains from Philox initial orders, `steps` steps, then
+ *   best_order  n uint8       the best order over all chains
+ *   best_dag    n x n uint8   its greedy DAG, best_dag[i*n + m] = 1 iff m -> i
+ *   best_score  1 float64
+ *   edge_freq   n x n float64 fraction of post-burn-in steps (all chains) with m -> i
+ * Any output may be NULL.  Outputs are host memory. */
+int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
+                uint8_t* best_order, uint8_t* best_dag, double* best_score,
+                double* edge_freq, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Misc                                                                                */
+/* ---------------------------------------------------------------------------------- */
+
+const char* bn_last_error(void);     /* thread-local; "" when no error                 */
+const char* bn_version(void);
+/* Number of kernel launches the library issued on behalf of the calling process so far
+ * (graph replays count their kernel nodes). */
+int64_t bn_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BN_H */

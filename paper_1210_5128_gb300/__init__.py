@@ -1,0 +1,338 @@
+"""Python binding of libbngpu.so, the GB300 order-space Bayesian-network scorer.
+
+Argument marshalling only: every step runs in the library's CUDA kernels behind the C
+ABI declared in include/bn.h, and the names here are the C names without the ``bn_``
+prefix.  Arrays may be numpy arrays / CPU tensors (host memory, results come back as
+numpy arrays) or CUDA tensors (device memory, results are CUDA tensors on the same
+device and the call runs on torch's current stream).
+
+There is no CPU fallback: if the shared library is missing or cannot be loaded the
+import fails with the reason.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbngpu.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+MEM_HOST, MEM_DEVICE = 0, 1
+OUT = dict(orders=1, scores=2, ranks=3, best_orders=4, best_scores=5, best_ranks=6,
+           edge_counts=7, accepts=8, trace_score=9, trace_accept=10, steps=11, ess=12, record=13,
+           record_len=14)
+
+# names the ABI exports (include/bn.h); tests check the library against this list
+ABI = ["bn_build_scores", "bn_table_from_scores", "bn_table_info", "bn_table_scores",
+       "bn_table_free", "bn_score_orders", "bn_unrank", "bn_rank", "bn_chains_create",
+       "bn_chains_step", "bn_chains_step_profiled", "bn_chains_read", "bn_chains_free",
+       "bn_mcmc_run", "bn_last_error", "bn_version", "bn_kernel_launches"]
+
+
+class BNError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class ScoreParams(C.Structure):
+    _fields_ = [("score_kind", C.c_int), ("ess", C.c_double), ("log10_gamma", C.c_double)]
+
+
+class MCMCParams(C.Structure):
+    _fields_ = [("chains", C.c_int), ("burn_in", C.c_int64), ("seed", C.c_uint64),
+                ("literal_log", C.c_int), ("record_every", C.c_int), ("record_cap", C.c_int),
+                ("trace", C.c_int), ("trace_cap", C.c_int64)]
+
+
+_vp = C.c_void_p
+_L = None
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbngpu.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    _L = C.CDLL(LIB_PATH)
+    _L.bn_last_error.restype = C.c_char_p
+    _L.bn_version.restype = C.c_char_p
+    _L.bn_kernel_launches.restype = C.c_int64
+    _L.bn_build_scores.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, C.POINTER(ScoreParams),
+                                   C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_table_from_scores.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_table_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]
+    _L.bn_table_scores.argtypes = [_vp, C.c_int, _vp, C.c_int, _vp]
+    _L.bn_table_free.argtypes = [_vp]
+    _L.bn_table_free.restype = None
+    _L.bn_score_orders.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp]
+    _L.bn_unrank.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_uint64)]
+    _L.bn_rank.argtypes = [C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_int64)]
+    _L.bn_chains_create.argtypes = [_vp, C.POINTER(MCMCParams), _vp, C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_chains_step.argtypes = [_vp, C.c_int64, _vp]
+    _L.bn_chains_step_profiled.argtypes = [_vp, C.c_int64, _vp, C.POINTER(C.c_double),
+                                               C.POINTER(C.c_int64)]
+    _L.bn_chains_read.argtypes = [_vp, C.c_int, _vp, C.c_int, _vp]
+    _L.bn_chains_free.argtypes = [_vp]
+    _L.bn_chains_free.restype = None
+    _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp, _vp]
+    return _L
+
+
+def lib():
+    """The loaded C library (loaded on first use; raises if it is not built)."""
+    global _L
+    if _L is None:
+        _L = _load()
+    return _L
+
+
+def last_error() -> str:
+    return lib().bn_last_error().decode()
+
+
+def version() -> str:
+    return lib().bn_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(lib().bn_kernel_launches())
+
+
+def _check(rc):
+    if rc != OK:
+        raise BNError(rc, last_error())
+
+
+# ---- marshalling ---------------------------------------------------------------------
+def _is_cuda(x):
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _stream(dev_tensor):
+    if dev_tensor is None:
+        return None
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(dev_tensor.device).cuda_stream)
+
+
+def _host(x, dtype):
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _dev(x, tdtype):
+    if x.dtype != tdtype:
+        x = x.to(tdtype)
+    return x.contiguous()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Table:
+    """Owns a bn_table*; freed with the object (or explicitly with free())."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("table already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().bn_table_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        return table_info(self)
+
+
+def build_scores(data, arity, k, R=None, score_kind=0, ess=1.0, log10_gamma=0.0) -> Table:
+    """Local-score table of Eq. (4) + prior of Eq. (9) (bn_build_scores)."""
+    p = ScoreParams(score_kind, ess, log10_gamma)
+    h = _vp()
+    if _is_cuda(data):
+        import torch
+        d = _dev(data, torch.uint8)
+        a = _dev(arity.to(d.device) if hasattr(arity, "to") else torch.as_tensor(np.asarray(arity, np.uint8),
+                                                                                 device=d.device), torch.uint8)
+        r = None
+        if R is not None:
+            r = _dev(R.to(d.device) if hasattr(R, "to") else torch.as_tensor(np.asarray(R, np.float64),
+                                                                             device=d.device), torch.float64)
+        m, n = d.shape
+        _check(lib().bn_build_scores(_ptr(d), m, n, _ptr(a), k, _ptr(r), C.byref(p), MEM_DEVICE,
+                                  _stream(d), C.byref(h)))
+    else:
+        d = _host(data, np.uint8)
+        if d.ndim != 2:
+            raise ValueError("data must be (m, n)")
+        a = _host(arity, np.uint8)
+        r = _host(R, np.float64) if R is not None else None
+        m, n = d.shape
+        _check(lib().bn_build_scores(_ptr(d), m, n, _ptr(a), k, _ptr(r), C.byref(p), MEM_HOST,
+                                  None, C.byref(h)))
+    return Table(h)
+
+
+def table_from_scores(scores, k) -> Table:
+    h = _vp()
+    if _is_cuda(scores):
+        import torch
+        s = _dev(scores, torch.float64)
+        _check(lib().bn_table_from_scores(_ptr(s), s.shape[0], k, MEM_DEVICE, _stream(s), C.byref(h)))
+    else:
+        s = _host(scores, np.float64)
+        _check(lib().bn_table_from_scores(_ptr(s), s.shape[0], k, MEM_HOST, None, C.byref(h)))
+    return Table(h)
+
+
+def table_info(t: Table):
+    n, k, S, b = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+    _check(lib().bn_table_info(t.handle, C.byref(n), C.byref(k), C.byref(S), C.byref(b)))
+    return dict(n=n.value, k=k.value, sets_per_node=S.value, device_bytes=b.value)
+
+
+def table_scores(t: Table, node: int = -1, device=None):
+    info = table_info(t)
+    rows = info["n"] if node < 0 else 1
+    shape = (rows, info["sets_per_node"]) if node < 0 else (info["sets_per_node"],)
+    if device is not None:
+        import torch
+        out = torch.empty(shape, dtype=torch.float64, device=device)
+        _check(lib().bn_table_scores(t.handle, node, _ptr(out), MEM_DEVICE, _stream(out)))
+        return out
+    out = np.empty(shape, np.float64)
+    _check(lib().bn_table_scores(t.handle, node, _ptr(out), MEM_HOST, None))
+    return out
+
+
+def score_orders(t: Table, orders):
+    """Eq. (6) for a batch of orders (bn_score_orders) -> (best_rank (B,n), score (B,))."""
+    n = table_info(t)["n"]
+    if _is_cuda(orders):
+        import torch
+        o = _dev(orders, torch.uint8)
+        B = o.shape[0]
+        br = torch.empty((B, n), dtype=torch.int32, device=o.device)
+        sc = torch.empty((B,), dtype=torch.float64, device=o.device)
+        _check(lib().bn_score_orders(t.handle, _ptr(o), B, _ptr(br), _ptr(sc), MEM_DEVICE, _stream(o)))
+        return br, sc
+    o = _host(orders, np.uint8).reshape(-1, n)
+    B = o.shape[0]
+    br = np.empty((B, n), np.uint32)
+    sc = np.empty((B,), np.float64)
+    _check(lib().bn_score_orders(t.handle, _ptr(o), B, _ptr(br), _ptr(sc), MEM_HOST, None))
+    return br, sc
+
+
+def unrank(N, k, rank) -> int:
+    m = C.c_uint64()
+    _check(lib().bn_unrank(N, k, rank, C.byref(m)))
+    return m.value
+
+
+def rank(N, k, mask) -> int:
+    r = C.c_int64()
+    _check(lib().bn_rank(N, k, mask, C.byref(r)))
+    return r.value
+
+
+# ---- sampler -------------------------------------------------------------------------
+class Chains:
+    def __init__(self, handle, table, n, params):
+        self._h = handle
+        self.table = table          # keeps the table alive
+        self.n = n
+        self.params = params
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("chains already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().bn_chains_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def chains_create(t: Table, chains, seed, burn_in=0, init_orders=None, literal_log=False,
+                  record_every=0, record_cap=0, trace_cap=0) -> Chains:
+    n = table_info(t)["n"]
+    p = MCMCParams(chains, burn_in, seed, 1 if literal_log else 0, record_every, record_cap,
+                   1 if trace_cap else 0, trace_cap)
+    h = _vp()
+    io = _host(init_orders, np.uint8) if init_orders is not None else None
+    _check(lib().bn_chains_create(t.handle, C.byref(p), _ptr(io), MEM_HOST, None, C.byref(h)))
+    return Chains(h, t, n, p)
+
+
+def chains_step(c: Chains, steps: int, stream=None):
+    _check(lib().bn_chains_step(c.handle, steps, stream))
+
+
+def chains_step_profiled(c: Chains, steps: int, stream=None):
+    """Returns (summed scan-kernel ms, scan launches) measured with CUDA events."""
+    ms, nl = C.c_double(), C.c_int64()
+    _check(lib().bn_chains_step_profiled(c.handle, steps, stream, C.byref(ms), C.byref(nl)))
+    return ms.value, nl.value
+
+
+_OUT_SHAPES = {
+    "orders": (np.uint8, "cn"), "scores": (np.float64, "c"), "ranks": (np.uint32, "cn"),
+    "best_orders": (np.uint8, "cn"), "best_scores": (np.float64, "c"),
+    "best_ranks": (np.uint32, "cn"), "edge_counts": (np.uint32, "cnn"),
+    "accepts": (np.int64, "c"), "trace_score": (np.float64, "ct"),
+    "trace_accept": (np.uint8, "ct"), "steps": (np.int64, "1"), "ess": (np.float64, "nn"),
+    "record": (np.uint64, "cnnw"), "record_len": (np.int64, "1"),
+}
+
+
+def chains_read(c: Chains, what: str):
+    dtype, dims = _OUT_SHAPES[what]
+    size = {"c": c.params.chains, "n": c.n, "t": c.params.trace_cap, "1": 1,
+            "w": max(1, (c.params.record_cap + 63) // 64) if c.params.record_every > 0 else 0}
+    shape = tuple(size[d] for d in dims)
+    out = np.empty(shape, dtype)
+    _check(lib().bn_chains_read(c.handle, OUT[what], _ptr(out), MEM_HOST, None))
+    return out
+
+
+def mcmc_run(t: Table, chains, steps, seed, burn_in=0, literal_log=False):
+    """Algorithm 1 end to end (bn_mcmc_run): best order, its greedy DAG, best score and
+    edge frequencies."""
+    n = table_info(t)["n"]
+    p = MCMCParams(chains, burn_in, seed, 1 if literal_log else 0, 0, 0, 0, 0)
+    bo = np.empty(n, np.uint8)
+    dag = np.empty((n, n), np.uint8)
+    bs = np.empty(1, np.float64)
+    ef = np.empty((n, n), np.float64)
+    _check(lib().bn_mcmc_run(t.handle, C.byref(p), steps, _ptr(bo), _ptr(dag), _ptr(bs), _ptr(ef), None))
+    return dict(best_order=bo, best_dag=dag, best_score=float(bs[0]), edge_freq=ef)

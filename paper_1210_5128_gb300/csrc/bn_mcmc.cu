@@ -1,0 +1,686 @@
+// bn_mcmc.cu -- Algorithm 1's iteration on the device: Metropolis-Hastings over node
+// orders with the two-position swap proposal of Sec. III.C, the order score of Eq. (6),
+// best-graph tracking and (after burn-in) edge counts of the current greedy DAG.
+//
+// The paper scores one order per iteration on the GPU and keeps the MH test, the
+// best-graph update and the proposal on the CPU (Sec. V.A), crossing the bus every
+// iteration.  Here every chain's state lives on the device and one step of all chains
+// is three kernels, captured once as a CUDA graph and replayed:
+//   k_propose  Philox draw, swap, and the work list of nodes whose predecessor sets
+//              changed (the nodes between the two swapped positions; all others keep
+//              their best parent sets, which is exact)
+//   k_scan     the order-score scan of those (node, chain) items
+//   k_accept   chunk combine, FP64 order score (ascending node id), MH test, best
+//              graph, edge counts, trace/ESS records; the last block advances the step
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bn_table.cuh"
+
+namespace bn {
+
+static constexpr double LN10 = 2.302585092994045684017991454684364208;
+
+struct ChainState {
+    int n, C, nchunk;
+    uint64_t seed;
+    int64_t burn_in;
+    int literal_log;
+    int64_t trace_cap;
+    int record_every, record_cap, rec_words;
+    const int64_t* keys;       // table
+    const uint64_t* pst;
+    int64_t Sp;
+    uint8_t* cur_order;        // C*n
+    uint32_t* cur_rank;        // C*n
+    int64_t* cur_key;          // C*n
+    double* cur_score;         // C
+    uint8_t* best_order;
+    uint32_t* best_rank;
+    double* best_score;
+    int64_t* accepts;
+    uint32_t* edge;            // C*n*n
+    uint8_t* prop_order;       // C*n
+    uint8_t* prop_ab;          // C*2
+    double* prop_u;            // C
+    uint32_t* list_count;      // n
+    uint64_t* list_pc;         // n*C
+    uint32_t* slot_of;         // C*n
+    ScanPartial* part;         // n*C*nchunk
+    int64_t* step;             // 1
+    uint32_t* status;          // 1
+    uint32_t* done;            // 1
+    double* trace_score;       // C*trace_cap
+    uint8_t* trace_accept;
+    uint64_t* rec_bits;        // C*n*n*rec_words
+    int64_t* rec_count;        // 1
+};
+
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+__device__ __forceinline__ uint64_t compress_pred(uint64_t pred, int i)
+{
+    uint64_t lowm = (i == 0) ? 0ull : ((1ull << i) - 1);
+    return (pred & lowm) | ((i + 1 < 64) ? ((pred >> (i + 1)) << i) : 0ull);
+}
+
+// initial orders: Fisher-Yates from the identity driven by the Philox init stream
+__global__ void k_init_orders(ChainState S)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S.C) return;
+    uint8_t o[MAXN];
+    for (int p = 0; p < S.n; ++p) o[p] = (uint8_t)p;
+    U64x4 buf;
+    int used = 4;
+    uint64_t blk = 0;
+    for (int i = S.n - 1; i >= 1; --i) {
+        if (used == 4) { buf = philox4x64(blk++, (uint64_t)c, 1, 0, S.seed, 0); used = 0; }
+        uint64_t x = buf.x[used++];
+        int j = (int)mulhi64(x, (uint64_t)(i + 1));
+        uint8_t tmp = o[i]; o[i] = o[j]; o[j] = tmp;
+    }
+    for (int p = 0; p < S.n; ++p) S.cur_order[(size_t)c * S.n + p] = o[p];
+}
+
+// combine the chunk partials of one (node, item)
+__device__ __forceinline__ void combine_parts(const ScanPartial* p, int nchunk, int64_t& bk, uint32_t& br)
+{
+    bk = KEY_NONE;
+    br = 0xffffffffu;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        ScanPartial q = p[ch];
+        if (q.key > bk || (q.key == bk && q.rank < br)) { bk = q.key; br = q.rank; }
+    }
+}
+
+// full scoring of the initial orders (items of node i are chains 0..C-1)
+__global__ void k_init_state(ChainState S)
+{
+    __shared__ int64_t s_key[8][MAXN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + warp;
+    if (c >= S.C) return;
+    for (int i = lane; i < S.n; i += 32) {
+        int64_t bk;
+        uint32_t br;
+        combine_parts(S.part + ((size_t)i * S.C + c) * S.nchunk, S.nchunk, bk, br);
+        s_key[warp][i] = bk;
+        S.cur_key[(size_t)c * S.n + i] = bk;
+        S.cur_rank[(size_t)c * S.n + i] = br;
+        S.best_rank[(size_t)c * S.n + i] = br;
+    }
+    for (int p = lane; p < S.n; p += 32) S.best_order[(size_t)c * S.n + p] = S.cur_order[(size_t)c * S.n + p];
+    __syncwarp();
+    if (lane == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < S.n; ++i) sum = __dadd_rn(sum, key_to_double(s_key[warp][i]));
+        S.cur_score[c] = sum;
+        S.best_score[c] = sum;
+        S.accepts[c] = 0;
+    }
+}
+
+// step 1: proposal and work lists
+__global__ void k_propose(ChainState S)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S.C) return;
+    const int n = S.n;
+    const int64_t t = *S.step;
+    const U64x4 x = philox4x64((uint64_t)t, (uint64_t)c, 0, 0, S.seed, 0);
+    const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
+    int a, b;
+    pair_decode(n, mulhi64(x.x[0], P), a, b);
+    const double u = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
+    uint8_t* po = S.prop_order + (size_t)c * n;
+    const uint8_t* co = S.cur_order + (size_t)c * n;
+    uint64_t prefix = 0;
+    for (int p = 0; p <= b; ++p) {
+        int v = (p == a) ? co[b] : (p == b) ? co[a] : co[p];
+        po[p] = (uint8_t)v;
+        if (p >= a) {
+            uint32_t slot = atomicAdd(&S.list_count[v], 1u);
+            S.list_pc[(size_t)v * S.C + slot] = compress_pred(prefix, v);
+            S.slot_of[(size_t)c * n + v] = slot;
+        }
+        prefix |= 1ull << v;
+    }
+    for (int p = b + 1; p < n; ++p) po[p] = co[p];
+    S.prop_ab[2 * c] = (uint8_t)a;
+    S.prop_ab[2 * c + 1] = (uint8_t)b;
+    S.prop_u[c] = u;
+}
+
+// step 3: combine, MH test, bookkeeping; the last block advances the step counter
+__global__ void k_accept(ChainState S)
+{
+    __shared__ int64_t s_key[8][MAXN];
+    __shared__ uint32_t s_rank[8][MAXN];
+    __shared__ int s_acc[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + warp;
+    const int n = S.n;
+    const int64_t t = *S.step;
+    if (c < S.C) {
+        const int a = S.prop_ab[2 * c], b = S.prop_ab[2 * c + 1];
+        const uint8_t* po = S.prop_order + (size_t)c * n;
+        for (int p = lane; p < n; p += 32) {
+            const int v = po[p];
+            int64_t bk;
+            uint32_t br;
+            if (p >= a && p <= b) {
+                const uint32_t slot = S.slot_of[(size_t)c * n + v];
+                combine_parts(S.part + ((size_t)v * S.C + slot) * S.nchunk, S.nchunk, bk, br);
+            } else {
+                bk = S.cur_key[(size_t)c * n + v];
+                br = S.cur_rank[(size_t)c * n + v];
+            }
+            s_key[warp][v] = bk;
+            s_rank[warp][v] = br;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            double s2 = 0.0;
+            for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(s_key[warp][i]));
+            const double s1 = S.cur_score[c];
+            const double delta = __dsub_rn(s2, s1);
+            const double lu = log(S.prop_u[c]);
+            const bool acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+            s_acc[warp] = acc ? 1 : 0;
+            if (acc) {
+                S.cur_score[c] = s2;
+                S.accepts[c] += 1;
+                if (s2 > S.best_score[c]) { S.best_score[c] = s2; s_acc[warp] = 2; }
+            }
+            if (t < S.trace_cap) {
+                S.trace_score[(size_t)c * S.trace_cap + t] = acc ? s2 : s1;
+                S.trace_accept[(size_t)c * S.trace_cap + t] = acc ? 1 : 0;
+            }
+        }
+        __syncwarp();
+        const int acc = s_acc[warp];
+        if (acc) {
+            for (int p = lane; p < n; p += 32) {
+                S.cur_order[(size_t)c * n + p] = po[p];
+                S.cur_key[(size_t)c * n + p] = s_key[warp][p];
+                S.cur_rank[(size_t)c * n + p] = s_rank[warp][p];
+                if (acc == 2) {
+                    S.best_order[(size_t)c * n + p] = po[p];
+                    S.best_rank[(size_t)c * n + p] = s_rank[warp][p];
+                }
+            }
+        }
+        if (t >= S.burn_in) {
+            const bool rec = S.record_every > 0 && ((t - S.burn_in) % S.record_every) == 0 &&
+                             (t - S.burn_in) / S.record_every < S.record_cap;
+            const int64_t ridx = rec ? (t - S.burn_in) / S.record_every : 0;
+            for (int i = lane; i < n; i += 32) {
+                uint32_t r = acc ? s_rank[warp][i] : S.cur_rank[(size_t)c * n + i];
+                if ((int64_t)r >= S.Sp) r = 0;          // only after a timed-out scan
+                uint64_t m = S.pst[r];
+                uint32_t* E = S.edge + ((size_t)c * n + i) * n;
+                while (m) {
+                    const int slot = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const int par = slot + (slot >= i ? 1 : 0);
+                    E[par] += 1u;
+                    if (rec) {
+                        S.rec_bits[(((size_t)c * n + i) * n + par) * S.rec_words + (ridx >> 6)] |= 1ull << (ridx & 63);
+                    }
+                }
+            }
+        }
+    }
+    // the last block to finish advances the step and clears the work lists
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t ticket = atomicAdd(S.done, 1u);
+        if (ticket == gridDim.x - 1) {
+            for (int i = 0; i < n; ++i) S.list_count[i] = 0;
+            if (t >= S.burn_in && S.record_every > 0 && ((t - S.burn_in) % S.record_every) == 0 &&
+                (t - S.burn_in) / S.record_every < S.record_cap)
+                *S.rec_count = (t - S.burn_in) / S.record_every + 1;
+            *S.step = t + 1;
+            *S.done = 0;
+            __threadfence();
+        }
+    }
+}
+
+// Geyer initial monotone sequence ESS of each recorded edge-indicator series, summed over
+// chains.  Autocovariances are exact integers: T^3 g_k = T^2 P_k - T S (S1_k + S2_k) + (T-k) S^2
+// with P_k = sum_t x_t x_{t+k}, S = sum x, S1_k = sum_{t<T-k} x_t, S2_k = sum_{t>=k} x_t.
+__device__ __forceinline__ int bit_at(const uint64_t* w, int64_t t) { return (int)((w[t >> 6] >> (t & 63)) & 1ull); }
+
+__device__ int64_t lag_products(const uint64_t* w, int words, int64_t T, int64_t k)
+{
+    // sum_{t=0}^{T-1-k} x_t x_{t+k}
+    int64_t s = 0;
+    const int64_t ws = k >> 6, bs = k & 63;
+    for (int64_t q = 0; q < words; ++q) {
+        const int64_t qs = q + ws;
+        if (qs >= words) break;
+        uint64_t sh = w[qs] >> bs;
+        if (bs && qs + 1 < words) sh |= w[qs + 1] << (64 - bs);
+        uint64_t v = w[q] & sh;
+        // keep only t with t + k < T
+        const int64_t t0 = q * 64;
+        const int64_t lim = T - k - t0;
+        if (lim <= 0) break;
+        if (lim < 64) v &= (1ull << lim) - 1;
+        s += __popcll(v);
+    }
+    return s;
+}
+
+__global__ void k_ess(const uint64_t* __restrict__ bits, int C, int n, int words, int64_t T, double* __restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;     // edge index i*n + m
+    if (e >= n * n) return;
+    if (T < 2) { out[e] = NAN; return; }
+    double total = 0.0;
+    bool any = false;
+    const double T3 = (double)T * (double)T * (double)T;
+    for (int c = 0; c < C; ++c) {
+        const uint64_t* w = bits + ((size_t)c * n * n + e) * words;
+        int64_t Ssum = 0;
+        for (int q = 0; q < words; ++q) Ssum += __popcll(w[q]);
+        if (Ssum == 0 || Ssum == T) continue;                  // constant series
+        // prefix counts for S1_k (first T-k) and S2_k (last T-k) computed incrementally
+        int64_t head = Ssum, tail = Ssum;                       // k = 0
+        auto gk = [&](int64_t k, int64_t P) -> double {
+            const __int128 v = (__int128)T * T * P - (__int128)T * Ssum * (head + tail) + (__int128)(T - k) * Ssum * Ssum;
+            return (double)v / T3;
+        };
+        const double g0 = gk(0, Ssum);
+        double sum = 0.0, prev = INFINITY;
+        for (int64_t j = 0; 2 * j + 1 < T; ++j) {
+            double g[2];
+            for (int h = 0; h < 2; ++h) {
+                const int64_t k = 2 * j + h;
+                if (k > 0) {
+                    head -= bit_at(w, T - k);                   // drop x_{T-k} from the first T-k
+                    tail -= bit_at(w, k - 1);                   // drop x_{k-1} from the last T-k
+                }
+                g[h] = (k == 0) ? g0 : gk(k, lag_products(w, words, T, k));
+            }
+            double G = g[0] + g[1];
+            if (!(G > 0.0)) break;
+            if (G > prev) G = prev;
+            sum += G;
+            prev = G;
+        }
+        const double sigma2 = -g0 + 2.0 * sum;
+        if (sigma2 > 0.0) { total += (double)T * g0 / sigma2; any = true; }
+    }
+    out[e] = any ? total : NAN;
+}
+
+__global__ void k_edge_freq(const uint32_t* __restrict__ edge, int C, int n, double denom, double* __restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    uint64_t s = 0;
+    for (int c = 0; c < C; ++c) s += edge[(size_t)c * n * n + e];
+    out[e] = denom > 0 ? (double)s / denom : 0.0;
+}
+
+// best chain (highest best score, lowest chain id on ties) and its greedy DAG
+__global__ void k_pick_best(const double* __restrict__ best_score, const uint8_t* __restrict__ best_order,
+                            const uint32_t* __restrict__ best_rank, const uint64_t* __restrict__ pst, int C, int n,
+                            uint8_t* __restrict__ out_order, uint8_t* __restrict__ out_dag, double* __restrict__ out_score)
+{
+    __shared__ int s_c;
+    if (threadIdx.x == 0) {
+        int bc = 0;
+        for (int c = 1; c < C; ++c)
+            if (best_score[c] > best_score[bc]) bc = c;
+        s_c = bc;
+        *out_score = best_score[bc];
+    }
+    __syncthreads();
+    const int bc = s_c;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        out_order[i] = best_order[(size_t)bc * n + i];
+        for (int m = 0; m < n; ++m) out_dag[(size_t)i * n + m] = 0;
+        uint64_t msk = pst[best_rank[(size_t)bc * n + i]];
+        while (msk) {
+            const int slot = __ffsll((long long)msk) - 1;
+            msk &= msk - 1;
+            out_dag[(size_t)i * n + slot + (slot >= i ? 1 : 0)] = 1;
+        }
+    }
+}
+
+}  // namespace bn
+
+using namespace bn;
+
+struct bn_chains {
+    const bn_table* t = nullptr;
+    bn_mcmc_params p{};
+    ChainState S{};
+    ScanPlan plan{};
+    void* block = nullptr;          // one device allocation holding all state
+    cudaGraphExec_t exec = nullptr;
+    int64_t steps = 0;
+    int dev = 0;
+};
+
+static int sweep_launch(bn_chains* ch, cudaStream_t s)
+{
+    const ChainState& S = ch->S;
+    k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
+    BN_LAUNCH_CHECK("k_propose");
+    int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.C, S.part, S.status, s);
+    if (rc) return rc;
+    k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);
+    BN_LAUNCH_CHECK("k_accept");
+    return BN_OK;
+}
+
+extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, const uint8_t* init_orders, int mem,
+                                void* stream, bn_chains** out)
+{
+    set_error(BN_OK, "");
+    if (!out) return set_error(BN_EINVAL, "bn_chains_create: out is NULL");
+    *out = nullptr;
+    if (!t || !p) return set_error(BN_EINVAL, "bn_chains_create: NULL table/params");
+    if (p->chains < 1 || p->chains > 65536) return set_error(BN_EINVAL, "bn_chains_create: chains=%d", p->chains);
+    if (p->burn_in < 0 || p->record_every < 0 || p->record_cap < 0 || p->trace_cap < 0)
+        return set_error(BN_EINVAL, "bn_chains_create: negative burn_in/record/trace");
+    if (mem != BN_MEM_HOST && mem != BN_MEM_DEVICE) return set_error(BN_EINVAL, "bn_chains_create: bad mem");
+    cudaStream_t s = (cudaStream_t)stream;
+    bn_chains* ch = new bn_chains();
+    ch->t = t;
+    ch->p = *p;
+    ch->dev = device_id();
+    const int n = t->n, C = p->chains;
+    ch->plan = plan_scan(t, C);
+    ChainState& S = ch->S;
+    S.n = n;
+    S.C = C;
+    S.nchunk = ch->plan.nchunk;
+    S.seed = p->seed;
+    S.burn_in = p->burn_in;
+    S.literal_log = p->literal_log;
+    S.trace_cap = p->trace ? p->trace_cap : 0;
+    S.record_every = p->record_cap > 0 ? p->record_every : 0;
+    S.record_cap = S.record_every > 0 ? p->record_cap : 0;
+    S.rec_words = (S.record_cap + 63) / 64;
+    S.keys = t->keys;
+    S.pst = t->pst;
+    S.Sp = t->Sp;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
+    const size_t Cn = (size_t)C * n;
+    size_t o_cur_order = take(Cn), o_cur_rank = take(4 * Cn), o_cur_key = take(8 * Cn), o_cur_score = take(8 * C);
+    size_t o_best_order = take(Cn), o_best_rank = take(4 * Cn), o_best_score = take(8 * C), o_acc = take(8 * C);
+    size_t o_edge = take(4 * Cn * n), o_prop_order = take(Cn), o_prop_ab = take(2 * C), o_prop_u = take(8 * C);
+    size_t o_cnt = take(4 * (size_t)n), o_pc = take(8 * Cn), o_slot = take(4 * Cn);
+    size_t o_part = take(sizeof(ScanPartial) * Cn * ch->plan.nchunk);
+    size_t o_step = take(8), o_status = take(4), o_done = take(4), o_rec_count = take(8);
+    size_t o_ts = take(8 * (size_t)C * S.trace_cap), o_ta = take((size_t)C * S.trace_cap);
+    size_t o_rec = take(8 * Cn * n * S.rec_words);
+    size_t o_init = take(mem == BN_MEM_HOST && init_orders ? Cn : 0);
+    cudaError_t e = cudaMalloc(&ch->block, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ch;
+        return set_error(BN_ENOMEM, "bn_chains_create: %zu bytes of chain state: %s", off, cudaGetErrorString(e));
+    }
+    uint8_t* B = (uint8_t*)ch->block;
+    S.cur_order = B + o_cur_order;
+    S.cur_rank = (uint32_t*)(B + o_cur_rank);
+    S.cur_key = (int64_t*)(B + o_cur_key);
+    S.cur_score = (double*)(B + o_cur_score);
+    S.best_order = B + o_best_order;
+    S.best_rank = (uint32_t*)(B + o_best_rank);
+    S.best_score = (double*)(B + o_best_score);
+    S.accepts = (int64_t*)(B + o_acc);
+    S.edge = (uint32_t*)(B + o_edge);
+    S.prop_order = B + o_prop_order;
+    S.prop_ab = B + o_prop_ab;
+    S.prop_u = (double*)(B + o_prop_u);
+    S.list_count = (uint32_t*)(B + o_cnt);
+    S.list_pc = (uint64_t*)(B + o_pc);
+    S.slot_of = (uint32_t*)(B + o_slot);
+    S.part = (ScanPartial*)(B + o_part);
+    S.step = (int64_t*)(B + o_step);
+    S.status = (uint32_t*)(B + o_status);
+    S.done = (uint32_t*)(B + o_done);
+    S.rec_count = (int64_t*)(B + o_rec_count);
+    S.trace_score = (double*)(B + o_ts);
+    S.trace_accept = B + o_ta;
+    S.rec_bits = (uint64_t*)(B + o_rec);
+
+    auto fail = [&](int rc) { bn_chains_free(ch); return rc; };
+    if (cudaMemsetAsync(ch->block, 0, off, s) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__));
+    if (init_orders) {
+        const uint8_t* src = init_orders;
+        if (mem == BN_MEM_HOST) {
+            if (cudaMemcpyAsync(B + o_init, init_orders, Cn, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return fail(cuda_fail(cudaGetLastError(), "copy init orders", __FILE__, __LINE__));
+            src = B + o_init;
+        }
+        if (cudaMemcpyAsync(S.cur_order, src, Cn, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(cuda_fail(cudaGetLastError(), "copy init orders", __FILE__, __LINE__));
+    } else {
+        k_init_orders<<<(C + 127) / 128, 128, 0, s>>>(S);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return fail(cuda_fail(le, "k_init_orders", __FILE__, __LINE__));
+        count_launches(1);
+    }
+    // full scoring of the initial orders through the node-major lists
+    int rc = launch_pred_lists(S.cur_order, C, n, S.list_pc, S.list_count, S.status, s);
+    if (rc) return fail(rc);
+    if ((rc = launch_scan(t, ch->plan, S.list_count, S.list_pc, C, S.part, S.status, s))) return fail(rc);
+    k_init_state<<<(C + 7) / 8, 256, 0, s>>>(S);
+    {
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return fail(cuda_fail(le, "k_init_state", __FILE__, __LINE__));
+        count_launches(1);
+    }
+    if (cudaMemsetAsync(S.list_count, 0, 4 * (size_t)n, s) != cudaSuccess)
+        return fail(cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__));
+    uint32_t st = 0;
+    if (cudaMemcpyAsync(&st, S.status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cuda_fail(cudaGetLastError(), "bn_chains_create sync", __FILE__, __LINE__));
+    if (st & STATUS_BADINPUT) return fail(set_error(BN_EINVAL, "bn_chains_create: an initial order is not a permutation"));
+    if (st & STATUS_TIMEOUT) return fail(set_error(BN_ETIMEOUT, "bn_chains_create: a bounded device wait expired"));
+    *out = ch;
+    return BN_OK;
+}
+
+extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
+{
+    set_error(BN_OK, "");
+    if (!ch) return set_error(BN_EINVAL, "bn_chains_step: NULL chains");
+    if (steps < 0) return set_error(BN_EINVAL, "bn_chains_step: steps < 0");
+    if (steps == 0) return BN_OK;
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t s = user;
+    cudaStream_t own = nullptr;
+    if (user == nullptr) {
+        BN_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        BN_CUDA(cudaDeviceSynchronize());
+        s = own;
+    }
+    struct Own {
+        cudaStream_t s;
+        ~Own()
+        {
+            if (s) cudaStreamDestroy(s);
+        }
+    } own_guard{own};
+    const int per_sweep = 3;
+    if (!ch->exec) {
+        cudaGraph_t g = nullptr;
+        BN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = sweep_launch(ch, s);
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+        cudaError_t ie = cudaGraphInstantiate(&ch->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate", __FILE__, __LINE__);
+        count_launches(-per_sweep);     // the captured launches did not run
+    }
+    for (int64_t i = 0; i < steps; ++i) BN_CUDA(cudaGraphLaunch(ch->exec, s));
+    count_launches(per_sweep * steps);
+    ch->steps += steps;
+    uint32_t st = 0;
+    BN_CUDA(cudaMemcpyAsync(&st, ch->S.status, 4, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_chains_step: a bounded device wait expired");
+    return BN_OK;
+}
+
+extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* stream, double* scan_ms,
+                                       int64_t* scan_launches)
+{
+    set_error(BN_OK, "");
+    if (!ch) return set_error(BN_EINVAL, "bn_chains_step_profiled: NULL chains");
+    if (steps < 0) return set_error(BN_EINVAL, "bn_chains_step_profiled: steps < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(2 * (size_t)steps);
+    for (auto& e : ev) BN_CUDA(cudaEventCreate(&e));
+    struct Ev {
+        std::vector<cudaEvent_t>& v;
+        ~Ev()
+        {
+            for (auto e : v) cudaEventDestroy(e);
+        }
+    } ev_guard{ev};
+    const ChainState& S = ch->S;
+    for (int64_t i = 0; i < steps; ++i) {
+        k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
+        BN_LAUNCH_CHECK("k_propose");
+        BN_CUDA(cudaEventRecord(ev[2 * i], s));
+        int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.C, S.part, S.status, s);
+        if (rc) return rc;
+        BN_CUDA(cudaEventRecord(ev[2 * i + 1], s));
+        k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);
+        BN_LAUNCH_CHECK("k_accept");
+    }
+    ch->steps += steps;
+    uint32_t st = 0;
+    BN_CUDA(cudaMemcpyAsync(&st, ch->S.status, 4, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    double tot = 0.0;
+    for (int64_t i = 0; i < steps; ++i) {
+        float ms = 0.f;
+        BN_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        tot += ms;
+    }
+    if (scan_ms) *scan_ms = tot;
+    if (scan_launches) *scan_launches = steps;
+    if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_chains_step_profiled: a bounded device wait expired");
+    return BN_OK;
+}
+
+extern "C" int bn_chains_read(const bn_chains* ch, int what, void* out, int mem, void* stream)
+{
+    set_error(BN_OK, "");
+    if (!ch || !out) return set_error(BN_EINVAL, "bn_chains_read: NULL argument");
+    if (mem != BN_MEM_HOST && mem != BN_MEM_DEVICE) return set_error(BN_EINVAL, "bn_chains_read: bad mem");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ChainState& S = ch->S;
+    const size_t Cn = (size_t)S.C * S.n;
+    const void* src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+        case BN_OUT_ORDERS: src = S.cur_order; bytes = Cn; break;
+        case BN_OUT_SCORES: src = S.cur_score; bytes = 8 * (size_t)S.C; break;
+        case BN_OUT_RANKS: src = S.cur_rank; bytes = 4 * Cn; break;
+        case BN_OUT_BEST_ORDERS: src = S.best_order; bytes = Cn; break;
+        case BN_OUT_BEST_SCORES: src = S.best_score; bytes = 8 * (size_t)S.C; break;
+        case BN_OUT_BEST_RANKS: src = S.best_rank; bytes = 4 * Cn; break;
+        case BN_OUT_EDGE_COUNTS: src = S.edge; bytes = 4 * Cn * S.n; break;
+        case BN_OUT_ACCEPTS: src = S.accepts; bytes = 8 * (size_t)S.C; break;
+        case BN_OUT_TRACE_SCORE: src = S.trace_score; bytes = 8 * (size_t)S.C * S.trace_cap; break;
+        case BN_OUT_TRACE_ACCEPT: src = S.trace_accept; bytes = (size_t)S.C * S.trace_cap; break;
+        case BN_OUT_STEPS: src = S.step; bytes = 8; break;
+        case BN_OUT_RECORD: src = S.rec_bits; bytes = 8 * Cn * S.n * S.rec_words; break;
+        case BN_OUT_RECORD_LEN: src = S.rec_count; bytes = 8; break;
+        case BN_OUT_ESS: {
+            int64_t T = 0;
+            BN_CUDA(cudaMemcpyAsync(&T, S.rec_count, 8, cudaMemcpyDeviceToHost, s));
+            BN_CUDA(cudaStreamSynchronize(s));
+            double* d = (double*)out;
+            double* tmp = nullptr;
+            if (mem == BN_MEM_HOST) {
+                BN_CUDA(cudaMallocAsync((void**)&tmp, 8 * (size_t)S.n * S.n, s));
+                d = tmp;
+            }
+            const int nn = S.n * S.n;
+            k_ess<<<(nn + 127) / 128, 128, 0, s>>>(S.rec_bits, S.C, S.n, std::max(S.rec_words, 1), T, d);
+            BN_LAUNCH_CHECK("k_ess");
+            if (mem == BN_MEM_HOST) {
+                BN_CUDA(cudaMemcpyAsync(out, tmp, 8 * (size_t)nn, cudaMemcpyDeviceToHost, s));
+                BN_CUDA(cudaFreeAsync(tmp, s));
+            }
+            BN_CUDA(cudaStreamSynchronize(s));
+            return BN_OK;
+        }
+        default: return set_error(BN_EINVAL, "bn_chains_read: unknown output %d", what);
+    }
+    if (bytes) BN_CUDA(cudaMemcpyAsync(out, src, bytes, mem == BN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    return BN_OK;
+}
+
+extern "C" void bn_chains_free(bn_chains* ch)
+{
+    if (!ch) return;
+    if (ch->exec) cudaGraphExecDestroy(ch->exec);
+    cudaFree(ch->block);
+    delete ch;
+}
+
+extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,
+                           uint8_t* best_dag, double* best_score, double* edge_freq, void* stream)
+{
+    set_error(BN_OK, "");
+    if (!t || !p || steps < 0) return set_error(BN_EINVAL, "bn_mcmc_run: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    bn_chains* ch = nullptr;
+    int rc = bn_chains_create(t, p, nullptr, BN_MEM_HOST, stream, &ch);
+    if (rc) return rc;
+    struct G {
+        bn_chains* c;
+        ~G() { bn_chains_free(c); }
+    } g{ch};
+    if ((rc = bn_chains_step(ch, steps, stream))) return rc;
+    const int n = t->n, C = p->chains;
+    uint8_t *d_o = nullptr, *d_dag = nullptr;
+    double *d_s = nullptr, *d_f = nullptr;
+    BN_CUDA(cudaMallocAsync((void**)&d_o, n, s));
+    BN_CUDA(cudaMallocAsync((void**)&d_dag, (size_t)n * n, s));
+    BN_CUDA(cudaMallocAsync((void**)&d_s, 8, s));
+    BN_CUDA(cudaMallocAsync((void**)&d_f, 8 * (size_t)n * n, s));
+    k_pick_best<<<1, 64, 0, s>>>(ch->S.best_score, ch->S.best_order, ch->S.best_rank, t->pst, C, n, d_o, d_dag, d_s);
+    BN_LAUNCH_CHECK("k_pick_best");
+    const double denom = (double)C * (double)std::max<int64_t>(0, steps - p->burn_in);
+    k_edge_freq<<<(n * n + 127) / 128, 128, 0, s>>>(ch->S.edge, C, n, denom, d_f);
+    BN_LAUNCH_CHECK("k_edge_freq");
+    if (best_order) BN_CUDA(cudaMemcpyAsync(best_order, d_o, n, cudaMemcpyDeviceToHost, s));
+    if (best_dag) BN_CUDA(cudaMemcpyAsync(best_dag, d_dag, (size_t)n * n, cudaMemcpyDeviceToHost, s));
+    if (best_score) BN_CUDA(cudaMemcpyAsync(best_score, d_s, 8, cudaMemcpyDeviceToHost, s));
+    if (edge_freq) BN_CUDA(cudaMemcpyAsync(edge_freq, d_f, 8 * (size_t)n * n, cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(d_o, s);
+    cudaFreeAsync(d_dag, s);
+    cudaFreeAsync(d_s, s);
+    cudaFreeAsync(d_f, s);
+    BN_CUDA(cudaStreamSynchronize(s));
+    return BN_OK;
+}

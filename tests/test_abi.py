@@ -1,0 +1,93 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol include/bn.h
+declares, and its host-only helpers and argument checks behave (no GPU work)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bn():
+    from paper_1210_5128_gb300 import build as b
+    b.build()
+    import paper_1210_5128_gb300 as mod
+    return mod
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_abi(bn):
+    decl = _declared()
+    assert set(bn.ABI) <= set(decl)
+    for name in decl:
+        assert hasattr(bn.lib(), name), f"{name} declared in bn.h but not exported"
+
+
+def test_exports_match_nm(bn):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", bn.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (bn_[a-z_0-9]+)$", out, flags=re.M))
+    assert set(_declared()) <= exported
+
+
+def test_version_and_error_string(bn):
+    assert "sm_103a" in bn.version()
+    assert isinstance(bn.last_error(), str)
+
+
+@pytest.mark.parametrize("N,k", [(5, 2), (19, 4), (59, 4), (63, 3)])
+def test_rank_helpers_match_oracle(bn, N, k):
+    rng = np.random.default_rng(N * 10 + k)
+    S = oracle.num_sets(N, k)
+    for r in list(range(min(S, 50))) + list(rng.integers(0, S, 200)) + [S - 1]:
+        r = int(r)
+        mask = bn.unrank(N, k, r)
+        assert [c for c in range(N) if mask >> c & 1] == oracle.unrank(N, k, r)
+        assert bn.rank(N, k, mask) == r
+
+
+def test_rank_helper_errors(bn):
+    with pytest.raises(bn.BNError) as e:
+        bn.unrank(5, 2, oracle.num_sets(5, 2))
+    assert e.value.code == bn.EINVAL
+    with pytest.raises(bn.BNError):
+        bn.rank(5, 2, 0b111)          # three bits > k
+    with pytest.raises(bn.BNError):
+        bn.rank(5, 2, 1 << 5)         # bit at N
+
+
+def test_argument_checks_before_any_device_work(bn):
+    L = bn.lib()
+    h = C.c_void_p()
+    data = np.zeros((4, 3), np.uint8)
+    ar = np.full(3, 2, np.uint8)
+    # n out of range, k out of range, arity out of range, NULL out
+    assert L.bn_build_scores(data.ctypes.data, 4, 1, ar.ctypes.data, 0, None, None, 0, None, C.byref(h)) == bn.EINVAL
+    assert L.bn_build_scores(data.ctypes.data, 4, 65, ar.ctypes.data, 0, None, None, 0, None, C.byref(h)) == bn.EINVAL
+    assert L.bn_build_scores(data.ctypes.data, 4, 3, ar.ctypes.data, 3, None, None, 0, None, C.byref(h)) == bn.EINVAL
+    bad = np.array([2, 5, 2], np.uint8)
+    assert L.bn_build_scores(data.ctypes.data, 4, 3, bad.ctypes.data, 1, None, None, 0, None, C.byref(h)) == bn.EINVAL
+    assert "arity" in bn.last_error()
+    d2 = data.copy()
+    d2[2, 1] = 2
+    assert L.bn_build_scores(d2.ctypes.data, 4, 3, ar.ctypes.data, 1, None, None, 0, None, C.byref(h)) == bn.EINVAL
+    R = np.full((3, 3), 0.5)
+    R[0, 1] = np.nan
+    assert L.bn_build_scores(data.ctypes.data, 4, 3, ar.ctypes.data, 1, R.ctypes.data, None, 0, None,
+                             C.byref(h)) == bn.EINVAL
+    R[0, 1] = 1.5
+    assert L.bn_build_scores(data.ctypes.data, 4, 3, ar.ctypes.data, 1, R.ctypes.data, None, 0, None,
+                             C.byref(h)) == bn.EINVAL
+    assert L.bn_build_scores(data.ctypes.data, 4, 3, ar.ctypes.data, 1, None, None, 0, None, None) == bn.EINVAL
+    assert L.bn_score_orders(None, None, 1, None, None, 0, None) == bn.EINVAL
+    assert L.bn_table_info(None, None, None, None, None) == bn.EINVAL
