@@ -110,6 +110,27 @@ void bn_table_free(bn_table* t);
 int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
                     double* order_score, int mem, void* stream);
 
+/* bn_score_orders without any allocation.  The paper has no counterpart to this call.
+ * It is for callers that cannot allocate device memory when they score orders: a host
+ * framework whose memory pool owns the device and forbids outside allocations, a
+ * latency-critical loop that cannot take the implicit device synchronisation of
+ * cudaMalloc/cudaFree, a plugin handed pre-allocated buffers only.
+ *   orders, best_rank, order_score: DEVICE pointers, same layouts as bn_score_orders
+ *   (best_rank and order_score may be NULL).
+ * The work lists and partial results live in one static 8 MiB device array that every
+ * GPU loading the library holds until the process exits; B is limited to what fits
+ * (about 8 MiB / (24 n) orders: 5,800 at n = 60), larger B returns BN_EINVAL with the
+ * limit in the message.  Nothing is allocated or freed: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the previous call's
+ * contents (the call clears what must start at zero), so calls that overlap on the GPU
+ * (other streams, other host threads) race: serialise them.
+ * Errors: as bn_score_orders. */
+int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
+                            uint32_t* best_rank, double* order_score, void* stream);
+
 /* Candidate-space mask of a rank and back (host-side helpers, no GPU needed).
  * mask bit c = candidate slot c.  Errors: BN_EINVAL if rank >= S(N,k) or the mask has
  * more than k bits or bits at or above N. */

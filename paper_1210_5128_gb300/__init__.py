@@ -69,6 +69,7 @@ def _load():
     _L.bn_table_free.argtypes = [_vp]
     _L.bn_table_free.restype = None
     _L.bn_score_orders.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp]
+    _L.bn_score_orders_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
     _L.bn_unrank.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_uint64)]
     _L.bn_rank.argtypes = [C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_int64)]
     _L.bn_chains_create.argtypes = [_vp, C.POINTER(MCMCParams), _vp, C.c_int, _vp, C.POINTER(_vp)]
