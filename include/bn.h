@@ -119,7 +119,7 @@ int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* b
  *   (best_rank and order_score may be NULL).
  * The work lists and partial results live in one static 8 MiB device array that every
  * GPU loading the library holds until the process exits; B is limited to what fits
- * (about 8 MiB / (24 n) orders: 5,800 at n = 60), larger B returns BN_EINVAL with the
+ * (about 8 MiB / (12 n) orders: 11,600 at n = 60), larger B returns BN_EINVAL with the
  * limit in the message.  Nothing is allocated or freed: no cudaMalloc, cudaFree or
  * allocating library routine.
  * The first call on each device looks up the array's device address

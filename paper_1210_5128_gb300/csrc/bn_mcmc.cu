@@ -24,7 +24,7 @@ namespace bn {
 static constexpr double LN10 = 2.302585092994045684017991454684364208;
 
 struct ChainState {
-    int n, C, nchunk;
+    int n, C;
     uint64_t seed;
     int64_t burn_in;
     int literal_log;
@@ -32,6 +32,7 @@ struct ChainState {
     int record_every, record_cap, rec_words;
     const int64_t* keys;       // table
     const uint64_t* pst;
+    const uint32_t* srank;
     int64_t Sp;
     uint8_t* cur_order;        // C*n
     uint32_t* cur_rank;        // C*n
@@ -48,7 +49,7 @@ struct ChainState {
     uint32_t* list_count;      // n
     uint64_t* list_pc;         // n*C
     uint32_t* slot_of;         // C*n
-    ScanPartial* part;         // n*C*nchunk
+    uint32_t* list_best;       // n*C  scan results (sorted positions)
     int64_t* step;             // 1
     uint32_t* status;          // 1
     uint32_t* done;            // 1
@@ -85,15 +86,12 @@ __global__ void k_init_orders(ChainState S)
     for (int p = 0; p < S.n; ++p) S.cur_order[(size_t)c * S.n + p] = o[p];
 }
 
-// combine the chunk partials of one (node, item)
-__device__ __forceinline__ void combine_parts(const ScanPartial* p, int nchunk, int64_t& bk, uint32_t& br)
+// scan result of one (node, item): the chosen rank and its entry's key
+__device__ __forceinline__ void item_result(const ChainState& S, int i, uint32_t p, int64_t& bk, uint32_t& br)
 {
-    bk = KEY_NONE;
-    br = 0xffffffffu;
-    for (int ch = 0; ch < nchunk; ++ch) {
-        ScanPartial q = p[ch];
-        if (q.key > bk || (q.key == bk && q.rank < br)) { bk = q.key; br = q.rank; }
-    }
+    if ((int64_t)p >= S.Sp) p = 0;                     // only after a timed-out scan
+    br = S.srank[(size_t)i * S.Sp + p];
+    bk = S.keys[(size_t)i * S.Sp + br];
 }
 
 // full scoring of the initial orders (items of node i are chains 0..C-1)
@@ -106,7 +104,7 @@ __global__ void k_init_state(ChainState S)
     for (int i = lane; i < S.n; i += 32) {
         int64_t bk;
         uint32_t br;
-        combine_parts(S.part + ((size_t)i * S.C + c) * S.nchunk, S.nchunk, bk, br);
+        item_result(S, i, S.list_best[(size_t)i * S.C + c], bk, br);
         s_key[warp][i] = bk;
         S.cur_key[(size_t)c * S.n + i] = bk;
         S.cur_rank[(size_t)c * S.n + i] = br;
@@ -144,6 +142,7 @@ __global__ void k_propose(ChainState S)
         if (p >= a) {
             uint32_t slot = atomicAdd(&S.list_count[v], 1u);
             S.list_pc[(size_t)v * S.C + slot] = compress_pred(prefix, v);
+            S.list_best[(size_t)v * S.C + slot] = SPOS_NONE;
             S.slot_of[(size_t)c * n + v] = slot;
         }
         prefix |= 1ull << v;
@@ -173,7 +172,7 @@ __global__ void k_accept(ChainState S)
             uint32_t br;
             if (p >= a && p <= b) {
                 const uint32_t slot = S.slot_of[(size_t)c * n + v];
-                combine_parts(S.part + ((size_t)v * S.C + slot) * S.nchunk, S.nchunk, bk, br);
+                item_result(S, v, S.list_best[(size_t)v * S.C + slot], bk, br);
             } else {
                 bk = S.cur_key[(size_t)c * n + v];
                 br = S.cur_rank[(size_t)c * n + v];
@@ -376,7 +375,7 @@ static int sweep_launch(bn_chains* ch, cudaStream_t s)
     const ChainState& S = ch->S;
     k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
     BN_LAUNCH_CHECK("k_propose");
-    int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.C, S.part, S.status, s);
+    int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.list_best, S.C, S.status, s);
     if (rc) return rc;
     k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);
     BN_LAUNCH_CHECK("k_accept");
@@ -404,7 +403,6 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     ChainState& S = ch->S;
     S.n = n;
     S.C = C;
-    S.nchunk = ch->plan.nchunk;
     S.seed = p->seed;
     S.burn_in = p->burn_in;
     S.literal_log = p->literal_log;
@@ -414,6 +412,7 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     S.rec_words = (S.record_cap + 63) / 64;
     S.keys = t->keys;
     S.pst = t->pst;
+    S.srank = t->srank;
     S.Sp = t->Sp;
 
     size_t off = 0;
@@ -423,7 +422,7 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     size_t o_best_order = take(Cn), o_best_rank = take(4 * Cn), o_best_score = take(8 * C), o_acc = take(8 * C);
     size_t o_edge = take(4 * Cn * n), o_prop_order = take(Cn), o_prop_ab = take(2 * C), o_prop_u = take(8 * C);
     size_t o_cnt = take(4 * (size_t)n), o_pc = take(8 * Cn), o_slot = take(4 * Cn);
-    size_t o_part = take(sizeof(ScanPartial) * Cn * ch->plan.nchunk);
+    size_t o_best = take(4 * Cn);
     size_t o_step = take(8), o_status = take(4), o_done = take(4), o_rec_count = take(8);
     size_t o_ts = take(8 * (size_t)C * S.trace_cap), o_ta = take((size_t)C * S.trace_cap);
     size_t o_rec = take(8 * Cn * n * S.rec_words);
@@ -450,7 +449,7 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     S.list_count = (uint32_t*)(B + o_cnt);
     S.list_pc = (uint64_t*)(B + o_pc);
     S.slot_of = (uint32_t*)(B + o_slot);
-    S.part = (ScanPartial*)(B + o_part);
+    S.list_best = (uint32_t*)(B + o_best);
     S.step = (int64_t*)(B + o_step);
     S.status = (uint32_t*)(B + o_status);
     S.done = (uint32_t*)(B + o_done);
@@ -477,9 +476,9 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
         count_launches(1);
     }
     // full scoring of the initial orders through the node-major lists
-    int rc = launch_pred_lists(S.cur_order, C, n, S.list_pc, S.list_count, S.status, s);
+    int rc = launch_pred_lists(S.cur_order, C, n, S.list_pc, S.list_best, S.list_count, S.status, s);
     if (rc) return fail(rc);
-    if ((rc = launch_scan(t, ch->plan, S.list_count, S.list_pc, C, S.part, S.status, s))) return fail(rc);
+    if ((rc = launch_scan(t, ch->plan, S.list_count, S.list_pc, S.list_best, C, S.status, s))) return fail(rc);
     k_init_state<<<(C + 7) / 8, 256, 0, s>>>(S);
     {
         cudaError_t le = cudaGetLastError();
@@ -566,7 +565,7 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
         k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
         BN_LAUNCH_CHECK("k_propose");
         BN_CUDA(cudaEventRecord(ev[2 * i], s));
-        int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.C, S.part, S.status, s);
+        int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.list_best, S.C, S.status, s);
         if (rc) return rc;
         BN_CUDA(cudaEventRecord(ev[2 * i + 1], s));
         k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);

@@ -40,7 +40,8 @@ static int noalloc_scratch(void** out)
     return BN_OK;
 }
 
-__global__ void k_noalloc_reduce(const ScanPartial* __restrict__ part, int n, int cap, int nchunk, int B,
+__global__ void k_noalloc_reduce(const uint32_t* __restrict__ list_best, const uint32_t* __restrict__ srank,
+                                 const int64_t* __restrict__ keys, int64_t Sp, int n, int B,
                                  uint32_t* __restrict__ best_rank, double* __restrict__ score)
 {
     __shared__ int64_t s_key[8][MAXN];
@@ -48,15 +49,11 @@ __global__ void k_noalloc_reduce(const ScanPartial* __restrict__ part, int n, in
     const int b = blockIdx.x * (blockDim.x >> 5) + warp;
     if (b >= B) return;
     for (int i = lane; i < n; i += 32) {
-        const ScanPartial* p = part + ((size_t)i * cap + b) * nchunk;
-        int64_t bk = KEY_NONE;
-        uint32_t br = 0xffffffffu;
-        for (int c = 0; c < nchunk; ++c) {
-            const ScanPartial q = p[c];
-            if (q.key > bk || (q.key == bk && q.rank < br)) { bk = q.key; br = q.rank; }
-        }
-        s_key[warp][i] = bk;
-        if (best_rank) best_rank[(size_t)b * n + i] = br;
+        uint32_t p = list_best[(size_t)i * B + b];
+        if ((int64_t)p >= Sp) p = 0;                  // only after a timed-out scan
+        const uint32_t r = srank[(size_t)i * Sp + p];
+        s_key[warp][i] = keys[(size_t)i * Sp + r];
+        if (best_rank) best_rank[(size_t)b * n + i] = r;
     }
     __syncwarp();
     if (lane == 0 && score) {
@@ -81,25 +78,18 @@ extern "C" int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders,
     cudaStream_t s = (cudaStream_t)stream;
     const int n = t->n;
 
-    // fixed part of the scratch: status | counts | predecessor masks; the rest holds the
-    // partials, so the chunking is coarsened until they fit
+    // scratch: status | counts | predecessor masks | per-item results
     const size_t o_status = 0;
     const size_t o_cnt = 256;
     const size_t o_pc = (size_t)round_up((int64_t)(o_cnt + sizeof(uint32_t) * n), 256);
-    const size_t o_part = (size_t)round_up((int64_t)(o_pc + sizeof(uint64_t) * (size_t)n * B), 256);
-    const size_t per_chunk = sizeof(ScanPartial) * (size_t)n * B;
-    if (o_part + per_chunk > NOALLOC_SCRATCH_BYTES)
+    const size_t o_best = (size_t)round_up((int64_t)(o_pc + sizeof(uint64_t) * (size_t)n * B), 256);
+    const size_t need = o_best + sizeof(uint32_t) * (size_t)n * B;
+    if (need > NOALLOC_SCRATCH_BYTES)
         return set_error(BN_EINVAL,
                          "bn_score_orders_noalloc: B=%d orders of n=%d nodes need %zu bytes of scratch; the "
                          "static scratch holds %zu (at most %zu orders at this n)",
-                         B, n, o_part + per_chunk, NOALLOC_SCRATCH_BYTES,
-                         (NOALLOC_SCRATCH_BYTES - 1024 - 4 * (size_t)n) / ((sizeof(ScanPartial) + 8) * (size_t)n));
-    ScanPlan pl = plan_scan(t, B);
-    const int64_t max_chunks = (int64_t)((NOALLOC_SCRATCH_BYTES - o_part) / per_chunk);
-    if (pl.nchunk > max_chunks) {
-        pl.chunk = round_up((t->Sp + max_chunks - 1) / max_chunks, SUBQ);
-        pl.nchunk = (int)((t->Sp + pl.chunk - 1) / pl.chunk);
-    }
+                         B, n, need, NOALLOC_SCRATCH_BYTES, (NOALLOC_SCRATCH_BYTES - 1024 - 4 * (size_t)n) / (12 * (size_t)n));
+    const ScanPlan pl = plan_scan(t, B);
 
     void* base = nullptr;
     int rc = noalloc_scratch(&base);
@@ -108,14 +98,14 @@ extern "C" int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders,
     uint32_t* d_status = (uint32_t*)(sb + o_status);
     uint32_t* d_cnt = (uint32_t*)(sb + o_cnt);
     uint64_t* d_pc = (uint64_t*)(sb + o_pc);
-    ScanPartial* d_part = (ScanPartial*)(sb + o_part);
+    uint32_t* d_best = (uint32_t*)(sb + o_best);
 
     // the array keeps the previous call's contents: the status word must start at zero;
-    // counts, masks and partials are fully rewritten before they are read
+    // counts, masks and per-item results are rewritten by k_pred_lists before use
     BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
-    if ((rc = launch_pred_lists(orders, B, n, d_pc, d_cnt, d_status, s))) return rc;
-    if ((rc = launch_scan(t, pl, d_cnt, d_pc, B, d_part, d_status, s))) return rc;
-    k_noalloc_reduce<<<(B + 7) / 8, 256, 0, s>>>(d_part, n, B, pl.nchunk, B, best_rank, order_score);
+    if ((rc = launch_pred_lists(orders, B, n, d_pc, d_best, d_cnt, d_status, s))) return rc;
+    if ((rc = launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_status, s))) return rc;
+    k_noalloc_reduce<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, best_rank, order_score);
     BN_LAUNCH_CHECK("k_noalloc_reduce");
     uint32_t st = 0;
     BN_CUDA(cudaMemcpyAsync(&st, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -2,14 +2,18 @@
 //
 // For node i and an order, the best entry is the maximum of entry(i, rho) over the ranks
 // rho whose parent set lies inside the node's predecessors, ties to the lowest rank.
-// The paper assigns h blocks per node and splits one order's consistent sets over
-// their threads (Sec. V.B), then reduces an argmax in shared memory.  Here a block
-// owns a contiguous chunk of one node's table and a group of up to 256 (order, node)
-// work items, one per thread: the chunk is streamed once from HBM into shared memory
-// by 1-D bulk (TMA) copies, every thread tests each staged entry's candidate mask
-// against its item's predecessor mask and keeps a running (key, rank) maximum, so the
-// table is read once per group of 256 orders instead of once per order.  The per-chunk
-// results of one item are then combined (max key, lowest rank) by a small kernel.
+// With every entry's sorted position spos (score descending, rank ascending; unique per
+// node) that is the entry of minimum spos among the consistent ones.
+//
+// The paper assigns h blocks per node and splits one order's consistent sets over their
+// threads (Sec. V.B), then reduces an argmax in shared memory.  Here a block owns a
+// contiguous chunk of one node's table and up to 256 (order, node) work items, one per
+// thread.  The chunk's spos values and parent-set masks are streamed once into shared
+// memory by 1-D bulk (TMA) copies; every thread tests each staged entry's candidate mask
+// against its item's predecessor mask and keeps a running min of spos.  So the table is
+// read once per 256 orders instead of once per order, and a test is a 64-bit AND-NOT,
+// a zero test and one unsigned min.  When a block holds fewer than 256 items, its spare
+// warps take a share of the entries of the same items.  Chunks combine with atomicMin.
 #include <algorithm>
 #include <cstring>
 
@@ -18,76 +22,73 @@
 namespace bn {
 
 static constexpr int SCAN_THREADS = 256;
-static constexpr int SCAN_SUB = 1024;     // entries per shared-memory stage
-static constexpr int SCAN_STAGES = 3;
+static constexpr int SCAN_WARPS = SCAN_THREADS / 32;
+static constexpr int SCAN_SUB = 1024;      // entries per shared-memory stage
+static constexpr int SCAN_STAGES = 4;
+static constexpr size_t SCAN_SMEM =
+    (size_t)SCAN_STAGES * SCAN_SUB * (sizeof(uint32_t) + sizeof(uint64_t)) + 8 * SCAN_STAGES;
 
 struct ScanArgs {
-    const int64_t* keys;
+    const uint32_t* spos;
     const uint64_t* pst;
     int64_t Sp;
     int nchunk;
     int64_t chunk;
     const uint32_t* list_count;
     const uint64_t* list_pc;
+    uint32_t* list_best;
     int cap;
-    ScanPartial* part;
     uint32_t* status;
 };
 
 ScanPlan plan_scan(const bn_table* t, int max_items)
 {
     ScanPlan p;
-    p.group = SCAN_THREADS;
-    p.sub = SCAN_SUB;
-    p.stages = SCAN_STAGES;
-    int groups = std::max(1, (max_items + SCAN_THREADS - 1) / SCAN_THREADS);
-    int64_t units = t->Sp / SUBQ;
-    int64_t target = (int64_t)sm_count() * 4 * 2;     // two waves of four blocks per SM
+    const int groups = std::max(1, (max_items + SCAN_THREADS - 1) / SCAN_THREADS);
+    const int64_t units = t->Sp / SUBQ;
+    const int64_t target = (int64_t)sm_count() * 4 * 2;     // two waves of four blocks per SM
     int64_t nchunk = (target + (int64_t)t->n * groups - 1) / ((int64_t)t->n * groups);
     nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, units));
-    int64_t chunk = round_up((t->Sp + nchunk - 1) / nchunk, SUBQ);
+    const int64_t chunk = round_up((t->Sp + nchunk - 1) / nchunk, SUBQ);
     p.chunk = chunk;
     p.nchunk = (int)((t->Sp + chunk - 1) / chunk);
     return p;
 }
 
-__device__ __forceinline__ void scan_issue(const ScanArgs& A, int node, int64_t base, int64_t e1,
-                                           int64_t* s_key, uint64_t* s_msk, uint64_t* bar,
-                                           uint64_t pol_stream, uint64_t pol_keep)
+__device__ __forceinline__ void scan_issue(const ScanArgs& A, int node, int64_t base, int64_t e1, uint32_t* s_sp,
+                                           uint64_t* s_msk, uint64_t* bar, uint64_t pol_stream, uint64_t pol_keep)
 {
     const uint32_t cnt = (uint32_t)min((int64_t)SCAN_SUB, e1 - base);
-    const uint32_t bytes = cnt * 8u;
-    mbar_arrive_expect_tx(bar, 2u * bytes);
-    bulk_g2s(s_key, A.keys + (size_t)node * A.Sp + base, bytes, bar, pol_stream);
-    bulk_g2s(s_msk, A.pst + base, bytes, bar, pol_keep);
-}
-
-__device__ __forceinline__ void scan_test(int64_t key, uint64_t msk, uint64_t npc, uint32_t rank,
-                                          int64_t& best, uint32_t& brank)
-{
-    const bool ok = (msk & npc) == 0ull;
-    if (ok & (key > best)) { best = key; brank = rank; }
+    mbar_arrive_expect_tx(bar, cnt * 12u);
+    bulk_g2s(s_sp, A.spos + (size_t)node * A.Sp + base, cnt * 4u, bar, pol_stream);
+    bulk_g2s(s_msk, A.pst + base, cnt * 8u, bar, pol_keep);
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    int64_t* s_key = (int64_t*)smem;                                  // [STAGES][SUB]
-    uint64_t* s_msk = (uint64_t*)(smem + sizeof(int64_t) * SCAN_STAGES * SCAN_SUB);
-    uint64_t* bar = (uint64_t*)(smem + 2 * sizeof(int64_t) * SCAN_STAGES * SCAN_SUB);
+    uint64_t* s_msk = (uint64_t*)smem;                                          // [STAGES][SUB]
+    uint32_t* s_sp = (uint32_t*)(smem + sizeof(uint64_t) * SCAN_STAGES * SCAN_SUB);
+    uint64_t* bar = (uint64_t*)(smem + (sizeof(uint64_t) + sizeof(uint32_t)) * SCAN_STAGES * SCAN_SUB);
 
     const int node = blockIdx.x / A.nchunk;
     const int chunk = blockIdx.x - node * A.nchunk;
     const int cnt = (int)A.list_count[node];
     const int g0 = blockIdx.y * SCAN_THREADS;
-    if (g0 >= cnt) return;                                           // block-uniform
+    if (g0 >= cnt) return;                                                      // block-uniform
     const int64_t e0 = (int64_t)chunk * A.chunk;
     const int64_t e1 = min(e0 + A.chunk, A.Sp);
     if (e0 >= e1) return;
-    const int item = g0 + (int)threadIdx.x;
-    const bool active = item < cnt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // G warps' worth of items; the spare warps split the entries of the same items
+    const int here = min(SCAN_THREADS, cnt - g0);
+    const int G = (here + 31) >> 5;
+    const int split = SCAN_WARPS / G;
+    const int ig = warp % G, sp = warp / G;
+    const bool warp_on = sp < split;
+    const int item = g0 + ig * 32 + lane;
+    const bool active = warp_on && item < cnt;
     const uint64_t npc = active ? ~A.list_pc[(size_t)node * A.cap + item] : ~0ull;
-    const bool warp_active = __any_sync(0xffffffffu, active);
     const int nsub = (int)((e1 - e0 + SCAN_SUB - 1) / SCAN_SUB);
 
     uint64_t pol_stream = 0, pol_keep = 0;
@@ -100,36 +101,34 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < SCAN_STAGES && s < nsub; ++s)
-            scan_issue(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_key + s * SCAN_SUB, s_msk + s * SCAN_SUB,
-                       &bar[s], pol_stream, pol_keep);
+            scan_issue(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_sp + s * SCAN_SUB, s_msk + s * SCAN_SUB, &bar[s],
+                       pol_stream, pol_keep);
     }
 
-    int64_t b0 = KEY_NONE, b1 = KEY_NONE;
-    uint32_t r0 = 0xffffffffu, r1 = 0xffffffffu;
+    uint32_t b0 = SPOS_NONE, b1 = SPOS_NONE;
     int it = 0;
     bool timed_out = false;
     for (; it < nsub; ++it) {
         const int st = it % SCAN_STAGES;
         const uint32_t parity = (uint32_t)((it / SCAN_STAGES) & 1);
         const bool ok = mbar_wait_bounded(&bar[st], parity, WAIT_TIMEOUT_NS);
-        if (ok && warp_active) {
+        if (ok && warp_on) {
             const int64_t base = e0 + (int64_t)it * SCAN_SUB;
-            const int n_e = (int)min((int64_t)SCAN_SUB, e1 - base);
-            const longlong2* K = (const longlong2*)(s_key + st * SCAN_SUB);
+            const int pairs = (int)min((int64_t)SCAN_SUB, e1 - base) >> 1;
+            const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
             const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
-            uint32_t rank = (uint32_t)base;
 #pragma unroll 4
-            for (int e = 0; e < n_e; e += 2, rank += 2) {
-                const longlong2 kk = K[e >> 1];
-                const ulonglong2 mm = M[e >> 1];
-                scan_test(kk.x, mm.x, npc, rank, b0, r0);
-                scan_test(kk.y, mm.y, npc, rank + 1, b1, r1);
+            for (int j = sp; j < pairs; j += split) {
+                const uint2 pp = P[j];
+                const ulonglong2 mm = M[j];
+                if ((mm.x & npc) == 0ull) b0 = min(b0, pp.x);
+                if ((mm.y & npc) == 0ull) b1 = min(b1, pp.y);
             }
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
             const int64_t base = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
-            scan_issue(A, node, base, e1, s_key + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st], pol_stream,
+            scan_issue(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st], pol_stream,
                        pol_keep);
         }
     }
@@ -142,39 +141,32 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
         }
         return;
     }
-    if (b1 > b0 || (b1 == b0 && r1 < r0)) { b0 = b1; r0 = r1; }
-    if (active) {
-        ScanPartial p;
-        p.key = b0;
-        p.rank = r0;
-        p.pad = 0;
-        A.part[((size_t)node * A.cap + item) * A.nchunk + chunk] = p;
-    }
+    const uint32_t b = min(b0, b1);
+    if (active && b != SPOS_NONE) atomicMin(&A.list_best[(size_t)node * A.cap + item], b);
 }
 
 int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_count, const uint64_t* list_pc,
-                int cap, ScanPartial* part, uint32_t* status, cudaStream_t s)
+                uint32_t* list_best, int cap, uint32_t* status, cudaStream_t s)
 {
     ScanArgs A;
-    A.keys = t->keys;
+    A.spos = t->spos;
     A.pst = t->pst;
     A.Sp = t->Sp;
     A.nchunk = pl.nchunk;
     A.chunk = pl.chunk;
     A.list_count = list_count;
     A.list_pc = list_pc;
+    A.list_best = list_best;
     A.cap = cap;
-    A.part = part;
     A.status = status;
-    const size_t smem = 2 * sizeof(int64_t) * SCAN_STAGES * SCAN_SUB + sizeof(uint64_t) * SCAN_STAGES;
     static bool attr_set[64] = {false};
-    int d = device_id();
+    const int d = device_id();
     if (d < 64 && !attr_set[d]) {
-        BN_CUDA(cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BN_CUDA(cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCAN_SMEM));
         attr_set[d] = true;
     }
     dim3 grid((unsigned)(t->n * pl.nchunk), (unsigned)((cap + SCAN_THREADS - 1) / SCAN_THREADS));
-    k_scan<<<grid, SCAN_THREADS, smem, s>>>(A);
+    k_scan<<<grid, SCAN_THREADS, SCAN_SMEM, s>>>(A);
     BN_LAUNCH_CHECK("k_scan");
     return BN_OK;
 }
@@ -182,41 +174,46 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
 // a5: candidate-space predecessor masks, written straight into the node-major work
 // lists (item b of node i is order b); also checks each row is a permutation.
 __global__ void k_pred_lists(const uint8_t* __restrict__ orders, int B, int n, uint64_t* __restrict__ list_pc,
-                             uint32_t* __restrict__ list_count, uint32_t* status)
+                             uint32_t* __restrict__ list_best, uint32_t* __restrict__ list_count, uint32_t* status)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n && blockIdx.x == 0) list_count[idx] = (uint32_t)B;
     if (idx >= B * n) return;
-    int b = idx / n, i = idx - b * n;
+    const int b = idx / n, i = idx - b * n;
     const uint8_t* o = orders + (size_t)b * n;
     uint64_t pred = 0, seen = 0;
     bool found = false;
     for (int p = 0; p < n; ++p) {
-        int v = o[p];
-        if (v >= n) { atomicOr(status, STATUS_BADINPUT); return; }
+        const int v = o[p];
+        if (v >= n) {
+            atomicOr(status, STATUS_BADINPUT);
+            break;
+        }
         seen |= 1ull << v;
         if (v == i) found = true;
         else if (!found) pred |= 1ull << v;
     }
-    uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
     if (seen != full) atomicOr(status, STATUS_BADINPUT);
-    uint64_t lowm = (i == 0) ? 0ull : ((1ull << i) - 1);
-    uint64_t pc = (pred & lowm) | ((i + 1 < 64) ? ((pred >> (i + 1)) << i) : 0ull);
+    const uint64_t lowm = (i == 0) ? 0ull : ((1ull << i) - 1);
+    const uint64_t pc = (pred & lowm) | ((i + 1 < 64) ? ((pred >> (i + 1)) << i) : 0ull);
     list_pc[(size_t)i * B + b] = pc;
+    list_best[(size_t)i * B + b] = SPOS_NONE;
 }
 
-int launch_pred_lists(const uint8_t* orders, int B, int n, uint64_t* list_pc, uint32_t* list_count,
-                      uint32_t* status, cudaStream_t s)
+int launch_pred_lists(const uint8_t* orders, int B, int n, uint64_t* list_pc, uint32_t* list_best,
+                      uint32_t* list_count, uint32_t* status, cudaStream_t s)
 {
     const int tot = B * n;
-    k_pred_lists<<<(tot + 255) / 256, 256, 0, s>>>(orders, B, n, list_pc, list_count, status);
+    k_pred_lists<<<(tot + 255) / 256, 256, 0, s>>>(orders, B, n, list_pc, list_best, list_count, status);
     BN_LAUNCH_CHECK("k_pred_lists");
     return BN_OK;
 }
 
-// a7: per (order, node) combine the chunk partials (max key, then lowest rank); the
-// order score is the FP64 sum over nodes in ascending node id.
-__global__ void k_reduce_orders(const ScanPartial* __restrict__ part, int n, int cap, int nchunk, int B,
+// a7: per order, the chosen rank of every node and the FP64 sum over nodes in ascending
+// node id of their entries
+__global__ void k_reduce_orders(const uint32_t* __restrict__ list_best, const uint32_t* __restrict__ srank,
+                                const int64_t* __restrict__ keys, int64_t Sp, int n, int B,
                                 uint32_t* __restrict__ best_rank, double* __restrict__ score)
 {
     __shared__ int64_t s_key[8][MAXN];
@@ -224,15 +221,11 @@ __global__ void k_reduce_orders(const ScanPartial* __restrict__ part, int n, int
     const int b = blockIdx.x * (blockDim.x >> 5) + warp;
     if (b >= B) return;
     for (int i = lane; i < n; i += 32) {
-        const ScanPartial* p = part + ((size_t)i * cap + b) * nchunk;
-        int64_t bk = KEY_NONE;
-        uint32_t br = 0xffffffffu;
-        for (int c = 0; c < nchunk; ++c) {
-            ScanPartial q = p[c];
-            if (q.key > bk || (q.key == bk && q.rank < br)) { bk = q.key; br = q.rank; }
-        }
-        s_key[warp][i] = bk;
-        if (best_rank) best_rank[(size_t)b * n + i] = br;
+        uint32_t p = list_best[(size_t)i * B + b];
+        if ((int64_t)p >= Sp) p = 0;                  // only after a timed-out scan
+        const uint32_t r = srank[(size_t)i * Sp + p];
+        s_key[warp][i] = keys[(size_t)i * Sp + r];
+        if (best_rank) best_rank[(size_t)b * n + i] = r;
     }
     __syncwarp();
     if (lane == 0 && score) {
@@ -258,16 +251,19 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
     cudaStream_t s = (cudaStream_t)stream;
     const int n = t->n;
     const ScanPlan pl = plan_scan(t, B);
-    const size_t n_part = (size_t)n * B * pl.nchunk;
 
-    // one scratch block: orders | list_pc | counts | status | partials | ranks | scores
+    // one scratch block: orders | list_pc | list_best | counts | status | ranks | scores
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
     const size_t o_orders = take(mem == BN_MEM_HOST ? (size_t)B * n : 0);
     const size_t o_pc = take(sizeof(uint64_t) * (size_t)n * B);
+    const size_t o_best = take(sizeof(uint32_t) * (size_t)n * B);
     const size_t o_cnt = take(sizeof(uint32_t) * n);
     const size_t o_st = take(sizeof(uint32_t));
-    const size_t o_part = take(sizeof(ScanPartial) * n_part);
     const size_t o_rank = take(mem == BN_MEM_HOST && best_rank ? sizeof(uint32_t) * (size_t)B * n : 0);
     const size_t o_score = take(mem == BN_MEM_HOST && order_score ? sizeof(double) * B : 0);
     uint8_t* base = nullptr;
@@ -287,20 +283,20 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
         d_orders = base + o_orders;
     }
     uint64_t* d_pc = (uint64_t*)(base + o_pc);
+    uint32_t* d_best = (uint32_t*)(base + o_best);
     uint32_t* d_cnt = (uint32_t*)(base + o_cnt);
     uint32_t* d_st = (uint32_t*)(base + o_st);
-    ScanPartial* d_part = (ScanPartial*)(base + o_part);
     uint32_t* d_rank = mem == BN_MEM_HOST ? (best_rank ? (uint32_t*)(base + o_rank) : nullptr) : best_rank;
     double* d_score = mem == BN_MEM_HOST ? (order_score ? (double*)(base + o_score) : nullptr) : order_score;
     BN_CUDA(cudaMemsetAsync(d_st, 0, sizeof(uint32_t), s));
-    int rc = launch_pred_lists(d_orders, B, n, d_pc, d_cnt, d_st, s);
+    int rc = launch_pred_lists(d_orders, B, n, d_pc, d_best, d_cnt, d_st, s);
     if (rc) return rc;
-    rc = launch_scan(t, pl, d_cnt, d_pc, B, d_part, d_st, s);
-    if (rc) return rc;
-    k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(d_part, n, B, pl.nchunk, B, d_rank, d_score);
+    if ((rc = launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_st, s))) return rc;
+    k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, d_rank, d_score);
     BN_LAUNCH_CHECK("k_reduce_orders");
     if (mem == BN_MEM_HOST) {
-        if (best_rank) BN_CUDA(cudaMemcpyAsync(best_rank, d_rank, sizeof(uint32_t) * (size_t)B * n, cudaMemcpyDeviceToHost, s));
+        if (best_rank)
+            BN_CUDA(cudaMemcpyAsync(best_rank, d_rank, sizeof(uint32_t) * (size_t)B * n, cudaMemcpyDeviceToHost, s));
         if (order_score) BN_CUDA(cudaMemcpyAsync(order_score, d_score, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     }
     uint32_t st = 0;

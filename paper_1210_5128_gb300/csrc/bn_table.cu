@@ -276,15 +276,19 @@ static int table_alloc(int n, int k, bn_table** out)
     t->Sp = round_up(t->S, SUBQ);
     cudaError_t e = cudaMalloc(&t->keys, sizeof(int64_t) * (size_t)n * (size_t)t->Sp);
     if (e == cudaSuccess) e = cudaMalloc(&t->pst, sizeof(uint64_t) * (size_t)t->Sp);
+    if (e == cudaSuccess) e = cudaMalloc(&t->spos, sizeof(uint32_t) * (size_t)n * (size_t)t->Sp);
+    if (e == cudaSuccess) e = cudaMalloc(&t->srank, sizeof(uint32_t) * (size_t)n * (size_t)t->Sp);
     if (e != cudaSuccess) {
         cudaFree(t->keys);
         cudaFree(t->pst);
+        cudaFree(t->spos);
+        cudaFree(t->srank);
         delete t;
         cudaGetLastError();
         return set_error(BN_ENOMEM, "table allocation of %lld entries failed: %s",
                          (long long)((int64_t)n * num_sets_host(n - 1, k)), cudaGetErrorString(e));
     }
-    t->bytes = sizeof(int64_t) * (size_t)n * (size_t)t->Sp + sizeof(uint64_t) * (size_t)t->Sp;
+    t->bytes = (sizeof(int64_t) + 2 * sizeof(uint32_t)) * (size_t)n * (size_t)t->Sp + sizeof(uint64_t) * (size_t)t->Sp;
     *out = t;
     return BN_OK;
 }
@@ -553,6 +557,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
         default: rc = launch_build_kt<12>(A, smem_data, smem, grid, s); break;
     }
     if (rc) return rc;
+    if ((rc = rank_entries(t, s))) return rc;
     uint32_t st = 0;
     if ((rc = read_status(d_status, &st, s))) return rc;
     if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_build_scores: a data value is >= its arity");
@@ -591,6 +596,7 @@ extern "C" int bn_table_from_scores(const double* scores, int n, int k, int mem,
     if (e != cudaSuccess) { bn_table_free(t); return cuda_fail(e, "k_keys_from_scores", __FILE__, __LINE__); }
     count_launches(1);
     if ((rc = build_pst(t, s))) { bn_table_free(t); return rc; }
+    if ((rc = rank_entries(t, s))) { bn_table_free(t); return rc; }
     uint32_t st = 0;
     if ((rc = read_status(d_status, &st, s))) { bn_table_free(t); return rc; }
     if (st) { bn_table_free(t); return set_error(BN_EINVAL, "bn_table_from_scores: NaN or +inf score"); }
@@ -634,5 +640,7 @@ extern "C" void bn_table_free(bn_table* t)
     if (!t) return;
     cudaFree(t->keys);
     cudaFree(t->pst);
+    cudaFree(t->spos);
+    cudaFree(t->srank);
     delete t;
 }

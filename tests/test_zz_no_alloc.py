@@ -55,7 +55,7 @@ def test_noalloc_full_size_and_limit(gpu):
         assert np.array_equal(rank, ref_rank)
         assert np.array_equal(score, ref_score)
     # a batch beyond the static array is refused with a clear error, nothing launched
-    big = torch.zeros((7000, 60), dtype=torch.uint8, device="cuda")
-    rc = bn.lib().bn_score_orders_noalloc(t.handle, C.c_void_p(big.data_ptr()), 7000, None, None,
+    big = torch.zeros((12000, 60), dtype=torch.uint8, device="cuda")
+    rc = bn.lib().bn_score_orders_noalloc(t.handle, C.c_void_p(big.data_ptr()), 12000, None, None,
                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == bn.EINVAL and "scratch" in bn.last_error()
