@@ -217,6 +217,82 @@ int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
                 double* edge_freq, void* stream);
 
 /* ---------------------------------------------------------------------------------- */
+/* Learned swap proposal                                                               */
+/* ---------------------------------------------------------------------------------- */
+
+/* The paper proposes a new order by swapping two uniformly chosen nodes (Sec. III.C).
+ * The learned proposal replaces the uniform choice of the pair by a small network over
+ * the current order, used inside an exact MH ratio (forward and reverse proposal
+ * probabilities), so the target distribution is unchanged:
+ *   x      = concat over positions p of E[sigma(p)]        (E: n x d node embeddings)
+ *   h1     = relu(W1 x + b1),  h2 = relu(W2 h1 + b2)        (W1: H x (n d), W2: H x H)
+ *   logits = W3 h2 + b3                                     (W3: P x H, P = n(n-1)/2 pairs
+ *                                                            a < b, lexicographic)
+ *   q(pair | sigma) = (1 - eps) softmax(logits)[pair] + eps / P
+ * Dense layers run on the tensor cores with bf16 weights and activations and FP32
+ * accumulation; master weights, biases, softmax and Adam are FP32.
+ * Training target: a logged uniform-swap step (sigma, pair, delta) fits the pair's logit
+ * by binary cross-entropy to alpha = min(1, 10^delta), the swap's acceptance probability;
+ * the loss is the batch mean. */
+typedef struct bn_mlp bn_mlp;
+
+typedef struct {
+    int   d;          /* embedding width                                              */
+    int   hidden;     /* H, a positive multiple of 128                                */
+    int   batch_cap;  /* largest batch of orders a forward/backward call takes         */
+    float lr;         /* Adam learning rate                                           */
+    float beta1, beta2, adam_eps;   /* 0 = defaults 0.9, 0.999, 1e-8                  */
+} bn_mlp_params;
+
+/* Weights are FP32, row-major, unpadded (E n x d, W1 H x (n d), b1 H, W2 H x H, b2 H,
+ * W3 P x H, b3 P), host or device per `mem`; the network keeps its own copies. */
+int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, const float* W1,
+                  const float* b1, const float* W2, const float* b2, const float* W3,
+                  const float* b3, int mem, void* stream, bn_mlp** out);
+/* logits of B <= batch_cap orders: B x P float32 */
+int bn_mlp_forward(bn_mlp* m, const uint8_t* orders, int B, float* logits, int mem,
+                   void* stream);
+/* loss and gradients (kept inside; read them with bn_mlp_read) of B logged steps:
+ * orders B x n, pairs B uint32 (pair index), alpha B float32 in [0, 1] */
+int bn_mlp_loss_grad(bn_mlp* m, const uint8_t* orders, const uint32_t* pairs,
+                     const float* alpha, int B, float* loss, int mem, void* stream);
+/* one Adam step on every parameter with the last gradients */
+int bn_mlp_adam_step(bn_mlp* m, void* stream);
+#define BN_MLP_E 0
+#define BN_MLP_W1 1
+#define BN_MLP_B1 2
+#define BN_MLP_W2 3
+#define BN_MLP_B2 4
+#define BN_MLP_W3 5
+#define BN_MLP_B3 6
+#define BN_MLP_GRAD_E 7   /* + the tensor id above: its gradient */
+/* copy a parameter or gradient out (FP32, unpadded layout as in bn_mlp_create) */
+int bn_mlp_read(const bn_mlp* m, int what, float* out, int mem, void* stream);
+void bn_mlp_free(bn_mlp* m);
+
+/* Proposal of a chain set's subsequent steps:
+ *   BN_PROPOSAL_UNIFORM  the paper's uniform two-position swap (the default)
+ *   BN_PROPOSAL_LEARNED  the pair is drawn from q(. | sigma) of the (frozen) network m;
+ *                        the MH test becomes  ln u < ln10 (s' - s) + ln q(pair | sigma')
+ *                        - ln q(pair | sigma)  (the reverse move swaps the same pair)
+ *   BN_PROPOSAL_TRAIN    uniform swaps; after every step the network takes one Adam step
+ *                        on that step's proposals (sigma, pair, alpha = min(1, 10^delta))
+ * Random numbers of the learned draw: u = ((x2 >> 11) + 0.5) 2^-53 of the step's Philox
+ * block, inverted through the cumulative q in pair order.  m must have the chains' n and
+ * batch_cap >= chains; it must outlive the chains (or the next call here).  eps_mix in
+ * (0, 1] keeps every pair proposable.  Errors: BN_EINVAL, BN_ENOMEM, BN_ECUDA. */
+#define BN_PROPOSAL_UNIFORM 0
+#define BN_PROPOSAL_LEARNED 1
+#define BN_PROPOSAL_TRAIN   2
+int bn_chains_set_proposal(bn_chains* c, bn_mlp* m, int mode, double eps_mix, void* stream);
+
+/* C (M x N float32) = A (M x K bf16) * B (N x K bf16)^T on the tensor cores (tcgen05,
+ * TMEM accumulator); device pointers, row-major, M and N multiples of 128, K of 64.
+ * The proposal network's dense-layer GEMM, exposed for testing. */
+int bn_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
+                 void* stream);
+
+/* ---------------------------------------------------------------------------------- */
 /* Misc                                                                                */
 /* ---------------------------------------------------------------------------------- */
 

@@ -48,6 +48,13 @@ class MCMCParams(C.Structure):
                 ("trace", C.c_int), ("trace_cap", C.c_int64)]
 
 
+class MLPParams(C.Structure):
+    _fields_ = [("d", C.c_int), ("hidden", C.c_int), ("batch_cap", C.c_int), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("adam_eps", C.c_float)]
+
+
+MLP_TENSORS = ["E", "W1", "b1", "W2", "b2", "W3", "b3"]
+
 _vp = C.c_void_p
 _L = None
 
@@ -80,6 +87,15 @@ def _load():
     _L.bn_chains_free.argtypes = [_vp]
     _L.bn_chains_free.restype = None
     _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp, _vp]
+    _L.bn_mlp_create.argtypes = [C.c_int, C.POINTER(MLPParams)] + [_vp] * 7 + [C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, _vp]
+    _L.bn_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_int, _vp]
+    _L.bn_mlp_adam_step.argtypes = [_vp, _vp]
+    _L.bn_mlp_read.argtypes = [_vp, C.c_int, _vp, C.c_int, _vp]
+    _L.bn_mlp_free.argtypes = [_vp]
+    _L.bn_mlp_free.restype = None
+    _L.bn_gemm_bf16.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
+    _L.bn_chains_set_proposal.argtypes = [_vp, _vp, C.c_int, C.c_double, _vp]
     return _L
 
 
@@ -337,3 +353,89 @@ def mcmc_run(t: Table, chains, steps, seed, burn_in=0, literal_log=False):
     ef = np.empty((n, n), np.float64)
     _check(lib().bn_mcmc_run(t.handle, C.byref(p), steps, _ptr(bo), _ptr(dag), _ptr(bs), _ptr(ef), None))
     return dict(best_order=bo, best_dag=dag, best_score=float(bs[0]), edge_freq=ef)
+
+
+# ---- learned proposal ----------------------------------------------------------------
+class MLP:
+    """Owns a bn_mlp* (the learned swap proposal network)."""
+
+    def __init__(self, handle, n, d, hidden, cap):
+        self._h, self.n, self.d, self.hidden, self.cap = handle, n, d, hidden, cap
+        self.P = n * (n - 1) // 2
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("network already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().bn_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mlp_create(n, weights, hidden=512, d=32, batch_cap=256, lr=1e-3) -> MLP:
+    """weights: dict E, W1, b1, W2, b2, W3, b3 (float arrays, unpadded row-major)."""
+    p = MLPParams(d, hidden, batch_cap, lr, 0.0, 0.0, 0.0)
+    ws = [_host(weights[k], np.float32) for k in MLP_TENSORS]
+    h = _vp()
+    _check(lib().bn_mlp_create(n, C.byref(p), *[_ptr(w) for w in ws], MEM_HOST, None, C.byref(h)))
+    return MLP(h, n, d, hidden, batch_cap)
+
+
+def mlp_forward(m: MLP, orders):
+    o = _host(orders, np.uint8).reshape(-1, m.n)
+    out = np.empty((o.shape[0], m.P), np.float32)
+    _check(lib().bn_mlp_forward(m.handle, _ptr(o), o.shape[0], _ptr(out), MEM_HOST, None))
+    return out
+
+
+def mlp_loss_grad(m: MLP, orders, pairs, alpha):
+    o = _host(orders, np.uint8).reshape(-1, m.n)
+    pr = _host(pairs, np.uint32)
+    al = _host(alpha, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(lib().bn_mlp_loss_grad(m.handle, _ptr(o), _ptr(pr), _ptr(al), o.shape[0], _ptr(loss), MEM_HOST, None))
+    return float(loss[0])
+
+
+def mlp_adam_step(m: MLP):
+    _check(lib().bn_mlp_adam_step(m.handle, None))
+
+
+def mlp_read(m: MLP, name: str, grad=False):
+    shapes = {"E": (m.n, m.d), "W1": (m.hidden, m.n * m.d), "b1": (m.hidden,), "W2": (m.hidden, m.hidden),
+              "b2": (m.hidden,), "W3": (m.P, m.hidden), "b3": (m.P,)}
+    out = np.empty(shapes[name], np.float32)
+    what = MLP_TENSORS.index(name) + (7 if grad else 0)
+    _check(lib().bn_mlp_read(m.handle, what, _ptr(out), MEM_HOST, None))
+    return out
+
+
+PROPOSAL_UNIFORM, PROPOSAL_LEARNED, PROPOSAL_TRAIN = 0, 1, 2
+
+
+def chains_set_proposal(c: Chains, mlp, mode, eps_mix=0.1, stream=None):
+    """Proposal of the chains' next steps (bn_chains_set_proposal)."""
+    c.mlp = mlp                 # keeps the network alive with the chains
+    _check(lib().bn_chains_set_proposal(c.handle, mlp.handle if mlp is not None else None, mode, eps_mix,
+                                        stream))
+
+
+def gemm_bf16(A, B):
+    """C = A @ B.T on the tensor cores; A (M, K), B (N, K) bf16 CUDA tensors."""
+    import torch
+    assert A.is_cuda and A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().bn_gemm_bf16(_ptr(A), _ptr(B), _ptr(out), M, N, K, _stream(A)))
+    return out

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "bn_mlp.cuh"
 #include "bn_table.cuh"
 
 namespace bn {
@@ -57,6 +58,18 @@ struct ChainState {
     uint8_t* trace_accept;
     uint64_t* rec_bits;        // C*n*n*rec_words
     int64_t* rec_count;        // 1
+    // proposal (BN_PROPOSAL_*): learned draws and their log proposal probabilities
+    int mode;
+    int P;                     // n(n-1)/2
+    float eps_mix;
+    float* cur_lq;             // C*P  log q(. | current order)
+    float* prop_lq;            // C*P  log q(. | proposed order)
+    uint32_t* prop_pair;       // C
+    float* prop_lqf;           // C  log q(pair | current)
+    float* delta;              // C  s' - s of the last step (training target)
+    uint8_t* train_orders;     // C*n  pre-step orders of the last step
+    uint32_t* train_pairs;     // C
+    float* train_alpha;        // C
 };
 
 __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
@@ -187,7 +200,13 @@ __global__ void k_accept(ChainState S)
             const double s1 = S.cur_score[c];
             const double delta = __dsub_rn(s2, s1);
             const double lu = log(S.prop_u[c]);
-            const bool acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+            // learned proposal: ln q(pair | proposed) - ln q(pair | current)
+            const double corr = S.mode == BN_PROPOSAL_LEARNED
+                                    ? (double)S.prop_lq[(size_t)c * S.P + S.prop_pair[c]] - (double)S.prop_lqf[c]
+                                    : 0.0;
+            const bool acc = S.literal_log ? (lu < __dadd_rn(delta, corr))
+                                           : (lu < __dadd_rn(__dmul_rn(LN10, delta), corr));
+            if (S.delta) S.delta[c] = (float)delta;
             s_acc[warp] = acc ? 1 : 0;
             if (acc) {
                 S.cur_score[c] = s2;
@@ -201,6 +220,9 @@ __global__ void k_accept(ChainState S)
         }
         __syncwarp();
         const int acc = s_acc[warp];
+        if (acc && S.mode == BN_PROPOSAL_LEARNED) {
+            for (int j = lane; j < S.P; j += 32) S.cur_lq[(size_t)c * S.P + j] = S.prop_lq[(size_t)c * S.P + j];
+        }
         if (acc) {
             for (int p = lane; p < n; p += 32) {
                 S.cur_order[(size_t)c * n + p] = po[p];
@@ -248,6 +270,106 @@ __global__ void k_accept(ChainState S)
             __threadfence();
         }
     }
+}
+
+// learned proposal, step 1: draw the pair from the cached q(. | current order) by inverse
+// CDF (one warp per chain), then the same swap and work lists as k_propose
+__global__ void k_propose_learned(ChainState S)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= S.C) return;
+    const int n = S.n, P = S.P;
+    const int64_t t = *S.step;
+    const U64x4 x = philox4x64((uint64_t)t, (uint64_t)c, 0, 0, S.seed, 0);
+    const float* lq = S.cur_lq + (size_t)c * P;
+    const int blk = (P + 31) / 32;
+    const int j0 = lane * blk, j1 = min(P, j0 + blk);
+    float part = 0.f;
+    for (int j = j0; j < j1; ++j) part += expf(lq[j]);
+    float incl = part;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const float total = __shfl_sync(0xffffffffu, incl, 31);
+    const double u = __dmul_rn(__dadd_rn((double)(x.x[2] >> 11), 0.5), 0x1p-53);
+    const float target = (float)(u * (double)total);
+    const unsigned over = __ballot_sync(0xffffffffu, incl > target && j1 > j0);
+    int owner = over ? __ffs(over) - 1 : 31;
+    while (owner > 0 && (owner * blk >= P)) --owner;            // a lane that holds pairs
+    int pair = -1;
+    if (lane == owner) {
+        float cum = incl - part;
+        for (int j = j0; j < j1; ++j) {
+            cum += expf(lq[j]);
+            if (cum > target) { pair = j; break; }
+        }
+        if (pair < 0) pair = j1 - 1;
+    }
+    pair = __shfl_sync(0xffffffffu, pair, owner);
+    if (lane != 0) return;
+    int a, b;
+    pair_decode(n, (uint64_t)pair, a, b);
+    const double um = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
+    uint8_t* po = S.prop_order + (size_t)c * n;
+    const uint8_t* co = S.cur_order + (size_t)c * n;
+    uint64_t prefix = 0;
+    for (int p = 0; p <= b; ++p) {
+        const int v = (p == a) ? co[b] : (p == b) ? co[a] : co[p];
+        po[p] = (uint8_t)v;
+        if (p >= a) {
+            const uint32_t slot = atomicAdd(&S.list_count[v], 1u);
+            S.list_pc[(size_t)v * S.C + slot] = compress_pred(prefix, v);
+            S.list_best[(size_t)v * S.C + slot] = SPOS_NONE;
+            S.slot_of[(size_t)c * n + v] = slot;
+        }
+        prefix |= 1ull << v;
+    }
+    for (int p = b + 1; p < n; ++p) po[p] = co[p];
+    S.prop_ab[2 * c] = (uint8_t)a;
+    S.prop_ab[2 * c + 1] = (uint8_t)b;
+    S.prop_u[c] = um;
+    S.prop_pair[c] = (uint32_t)pair;
+    S.prop_lqf[c] = lq[pair];
+}
+
+// log q(. | order) of every chain from the network's logits (row stride ldl):
+// log((1 - eps) softmax + eps / P), one warp per chain
+__global__ void k_log_q(const float* __restrict__ L, int ldl, int C, int P, float eps, float* __restrict__ out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= C) return;
+    const float* l = L + (size_t)c * ldl;
+    float mx = -INFINITY;
+    for (int j = lane; j < P; j += 32) mx = fmaxf(mx, l[j]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    float s = 0.f;
+    for (int j = lane; j < P; j += 32) s += __expf(l[j] - mx);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float lse = mx + __logf(s);
+    const float w = 1.f - eps, e = eps / (float)P;
+    for (int j = lane; j < P; j += 32) out[(size_t)c * P + j] = __logf(w * __expf(l[j] - lse) + e);
+}
+
+// training batch of the last uniform step: the pre-step order (the proposal with the
+// pair swapped back), the pair index and alpha = min(1, 10^delta)
+__global__ void k_train_batch(ChainState S)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S.C) return;
+    const int n = S.n;
+    const int a = S.prop_ab[2 * c], b = S.prop_ab[2 * c + 1];
+    const uint8_t* po = S.prop_order + (size_t)c * n;
+    uint8_t* o = S.train_orders + (size_t)c * n;
+    for (int p = 0; p < n; ++p) o[p] = po[p == a ? b : p == b ? a : p];
+    S.train_pairs[c] = (uint32_t)(a * (2 * n - a - 1) / 2 + (b - a - 1));
+    const float d = S.delta[c];
+    S.train_alpha[c] = d >= 0.f ? 1.f : exp10f(d);
 }
 
 // Geyer initial monotone sequence ESS of each recorded edge-indicator series, summed over
@@ -365,20 +487,43 @@ struct bn_chains {
     ChainState S{};
     ScanPlan plan{};
     void* block = nullptr;          // one device allocation holding all state
+    void* prop_block = nullptr;     // learned-proposal buffers (bn_chains_set_proposal)
+    bn_mlp* mlp = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int per_sweep = 3;              // kernel launches per step
     int64_t steps = 0;
     int dev = 0;
 };
 
-static int sweep_launch(bn_chains* ch, cudaStream_t s)
+// one MH step of every chain; ev0/ev1 (optional) bracket the scan launch
+static int sweep_launch(bn_chains* ch, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
     const ChainState& S = ch->S;
-    k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
-    BN_LAUNCH_CHECK("k_propose");
-    int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.list_best, S.C, S.status, s);
+    const int64_t l0 = bn_kernel_launches();
+    int rc;
+    if (S.mode == BN_PROPOSAL_LEARNED) {
+        k_propose_learned<<<(S.C + 7) / 8, 256, 0, s>>>(S);
+        BN_LAUNCH_CHECK("k_propose_learned");
+        if ((rc = mlp_forward_dev(ch->mlp, S.prop_order, S.C, false, s))) return rc;
+        k_log_q<<<(S.C + 7) / 8, 256, 0, s>>>(ch->mlp->L, ch->mlp->Pp, S.C, S.P, S.eps_mix, S.prop_lq);
+        BN_LAUNCH_CHECK("k_log_q");
+    } else {
+        k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
+        BN_LAUNCH_CHECK("k_propose");
+    }
+    if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
+    rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.list_best, S.C, S.status, s);
     if (rc) return rc;
+    if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);
     BN_LAUNCH_CHECK("k_accept");
+    if (S.mode == BN_PROPOSAL_TRAIN) {
+        k_train_batch<<<(S.C + 127) / 128, 128, 0, s>>>(S);
+        BN_LAUNCH_CHECK("k_train_batch");
+        if ((rc = mlp_loss_grad_dev(ch->mlp, S.train_orders, S.train_pairs, S.train_alpha, S.C, s))) return rc;
+        if ((rc = mlp_adam_dev(ch->mlp, s))) return rc;
+    }
+    ch->per_sweep = (int)(bn_kernel_launches() - l0);
     return BN_OK;
 }
 
@@ -518,7 +663,6 @@ extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
             if (s) cudaStreamDestroy(s);
         }
     } own_guard{own};
-    const int per_sweep = 3;
     if (!ch->exec) {
         cudaGraph_t g = nullptr;
         BN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -532,10 +676,10 @@ extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
         cudaError_t ie = cudaGraphInstantiate(&ch->exec, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate", __FILE__, __LINE__);
-        count_launches(-per_sweep);     // the captured launches did not run
+        count_launches(-ch->per_sweep);     // the captured launches did not run
     }
     for (int64_t i = 0; i < steps; ++i) BN_CUDA(cudaGraphLaunch(ch->exec, s));
-    count_launches(per_sweep * steps);
+    count_launches(ch->per_sweep * steps);
     ch->steps += steps;
     uint32_t st = 0;
     BN_CUDA(cudaMemcpyAsync(&st, ch->S.status, 4, cudaMemcpyDeviceToHost, s));
@@ -560,16 +704,9 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
             for (auto e : v) cudaEventDestroy(e);
         }
     } ev_guard{ev};
-    const ChainState& S = ch->S;
     for (int64_t i = 0; i < steps; ++i) {
-        k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
-        BN_LAUNCH_CHECK("k_propose");
-        BN_CUDA(cudaEventRecord(ev[2 * i], s));
-        int rc = launch_scan(ch->t, ch->plan, S.list_count, S.list_pc, S.list_best, S.C, S.status, s);
+        int rc = sweep_launch(ch, s, ev[2 * i], ev[2 * i + 1]);
         if (rc) return rc;
-        BN_CUDA(cudaEventRecord(ev[2 * i + 1], s));
-        k_accept<<<(S.C + 7) / 8, 256, 0, s>>>(S);
-        BN_LAUNCH_CHECK("k_accept");
     }
     ch->steps += steps;
     uint32_t st = 0;
@@ -643,7 +780,71 @@ extern "C" void bn_chains_free(bn_chains* ch)
     if (!ch) return;
     if (ch->exec) cudaGraphExecDestroy(ch->exec);
     cudaFree(ch->block);
+    cudaFree(ch->prop_block);
     delete ch;
+}
+
+extern "C" int bn_chains_set_proposal(bn_chains* ch, bn_mlp* m, int mode, double eps_mix, void* stream)
+{
+    set_error(BN_OK, "");
+    if (!ch) return set_error(BN_EINVAL, "bn_chains_set_proposal: NULL chains");
+    if (mode != BN_PROPOSAL_UNIFORM && mode != BN_PROPOSAL_LEARNED && mode != BN_PROPOSAL_TRAIN)
+        return set_error(BN_EINVAL, "bn_chains_set_proposal: mode %d", mode);
+    ChainState& S = ch->S;
+    if (mode != BN_PROPOSAL_UNIFORM) {
+        if (!m) return set_error(BN_EINVAL, "bn_chains_set_proposal: the learned modes need a network");
+        if (m->n != S.n) return set_error(BN_EINVAL, "bn_chains_set_proposal: network n=%d, chains n=%d", m->n, S.n);
+        if (m->cap < S.C) return set_error(BN_EINVAL, "bn_chains_set_proposal: batch_cap %d < %d chains", m->cap, S.C);
+        if (!(eps_mix > 0.0 && eps_mix <= 1.0)) return set_error(BN_EINVAL, "bn_chains_set_proposal: eps_mix in (0, 1]");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ch->exec) {                                   // the step graph changes shape
+        cudaGraphExecDestroy(ch->exec);
+        ch->exec = nullptr;
+    }
+    S.P = S.n * (S.n - 1) / 2;
+    if (!ch->prop_block) {
+        const size_t C = (size_t)S.C, P = (size_t)S.P;
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            const size_t o = off;
+            off = (size_t)round_up((int64_t)(off + bytes), 256);
+            return o;
+        };
+        const size_t o_cur = take(4 * C * P), o_prop = take(4 * C * P), o_pair = take(4 * C), o_lqf = take(4 * C),
+                     o_delta = take(4 * C), o_to = take(C * S.n), o_tp = take(4 * C), o_ta = take(4 * C);
+        cudaError_t e = cudaMalloc(&ch->prop_block, off);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ch->prop_block = nullptr;
+            return set_error(BN_ENOMEM, "bn_chains_set_proposal: %zu bytes: %s", off, cudaGetErrorString(e));
+        }
+        uint8_t* B = (uint8_t*)ch->prop_block;
+        S.cur_lq = (float*)(B + o_cur);
+        S.prop_lq = (float*)(B + o_prop);
+        S.prop_pair = (uint32_t*)(B + o_pair);
+        S.prop_lqf = (float*)(B + o_lqf);
+        S.delta = (float*)(B + o_delta);
+        S.train_orders = B + o_to;
+        S.train_pairs = (uint32_t*)(B + o_tp);
+        S.train_alpha = (float*)(B + o_ta);
+        BN_CUDA(cudaMemsetAsync(ch->prop_block, 0, off, s));
+    }
+    ch->mlp = m;
+    S.mode = mode;
+    S.eps_mix = (float)eps_mix;
+    if (mode == BN_PROPOSAL_LEARNED) {
+        // q(. | current order) of every chain from the network as it is now
+        int rc = mlp_forward_dev(m, S.cur_order, S.C, false, s);
+        if (rc) return rc;
+        k_log_q<<<(S.C + 7) / 8, 256, 0, s>>>(m->L, m->Pp, S.C, S.P, S.eps_mix, S.cur_lq);
+        BN_LAUNCH_CHECK("k_log_q");
+    }
+    uint32_t st = 0;
+    BN_CUDA(cudaMemcpyAsync(&st, m ? m->status : S.status, 4, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_chains_set_proposal: a bounded device wait expired");
+    return BN_OK;
 }
 
 extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,

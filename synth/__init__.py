@@ -148,6 +148,22 @@ def workload(name: str, seed_offset: int = 0):
     return data, net.arity.copy(), w["k"], R, net
 
 
+def mlp_init_weights(n: int, d: int, H: int, seed: int) -> dict:
+    """Seeded initial weights of the swap-proposal network (uniform, fan-in scaled,
+    zero biases): E n x d, W1 H x (n d), W2 H x H, W3 P x H with P = n(n-1)/2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = n * (n - 1) // 2
+    return dict(
+        E=rng.uniform(-1, 1, (n, d)).astype(np.float32),
+        W1=(rng.uniform(-1, 1, (H, n * d)) / math.sqrt(n * d)).astype(np.float32),
+        b1=np.zeros(H, np.float32),
+        W2=(rng.uniform(-1, 1, (H, H)) / math.sqrt(H)).astype(np.float32),
+        b2=np.zeros(H, np.float32),
+        W3=(rng.uniform(-1, 1, (P, H)) / math.sqrt(H)).astype(np.float32),
+        b3=np.zeros(P, np.float32),
+    )
+
+
 def uneven_batch(count: int, seed: int):
     """Many networks of uneven size: n ~ U{10..60}, per-node arity ~ U{2,3,4},
     m log-uniform in [200, 5000], k in {3, 4}, in-degree <= 3."""

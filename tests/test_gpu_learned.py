@@ -1,0 +1,80 @@
+"""The learned swap proposal inside the MH ratio.
+
+Exactness: with any proposal network (here a random, far-from-uniform one) the chain
+must still sample the order posterior proportional to 10^score, so its edge frequencies
+must match the exact edge posteriors obtained by enumerating all 720 orders of the
+6-node workload with the oracle.  Gain: after training on the uniform sampler's own
+history the learned proposal must get its swaps accepted more often than uniform swaps."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _exact_edge_posterior(tab, k):
+    n = tab.shape[0]
+    orders = [np.array(o, np.uint8) for o in itertools.permutations(range(n))]
+    res = [oracle.order_score(tab, k, o) for o in orders]
+    sc = np.array([r[0] for r in res])
+    w = np.power(10.0, sc - sc.max())
+    w /= w.sum()
+    post = np.zeros((n, n))
+    for (s, br), p in zip(res, w):
+        post += p * oracle.greedy_dag(n, k, br)
+    return post
+
+
+def test_learned_proposal_keeps_the_posterior_n6(gpu):
+    data, arity, k, R, _ = synth.workload("n6_k2_m100", 7)
+    # a flatter posterior (fewer samples) so several orders carry weight
+    data = data[:30].copy()
+    tab = oracle.build_table(data, arity, k)
+    exact = _exact_edge_posterior(tab, k)
+    n, d, H = 6, 8, 128
+    w = synth.mlp_init_weights(n, d, H, 3)
+    w["W3"] *= 8.0                                  # strongly non-uniform pair preferences
+    w["b3"] = np.linspace(-3, 3, n * (n - 1) // 2).astype(np.float32)
+    net = gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=128)
+    t = gpu.table_from_scores(tab, k)
+    C, steps, burn = 128, 6000, 500
+    ch = gpu.chains_create(t, C, 99, burn_in=burn)
+    gpu.chains_set_proposal(ch, net, gpu.PROPOSAL_LEARNED, eps_mix=0.2)
+    gpu.chains_step(ch, steps)
+    f = gpu.chains_read(ch, "edge_counts").sum(0) / (C * (steps - burn))
+    assert np.abs(f - exact).max() < 0.02, np.abs(f - exact).max()
+    # the proposal really was far from uniform: the learned chains accept at a different
+    # rate than uniform ones on the same table
+    u = gpu.chains_create(t, C, 99, burn_in=burn)
+    gpu.chains_step(u, steps)
+    fu = gpu.chains_read(u, "edge_counts").sum(0) / (C * (steps - burn))
+    assert np.abs(fu - exact).max() < 0.02
+    acc_l = gpu.chains_read(ch, "accepts").mean() / steps
+    acc_u = gpu.chains_read(u, "accepts").mean() / steps
+    assert abs(acc_l - acc_u) > 0.01, (acc_l, acc_u)
+
+
+def test_training_on_history_raises_acceptance_n20(gpu):
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    n, d, H = 20, 32, 256
+    net = gpu.mlp_create(n, synth.mlp_init_weights(n, d, H, 4), hidden=H, d=d, batch_cap=256, lr=2e-3)
+    C = 256
+    ch = gpu.chains_create(t, C, 5)
+    gpu.chains_step(ch, 200)                                     # burn in with uniform swaps
+    gpu.chains_set_proposal(ch, net, gpu.PROPOSAL_TRAIN)
+    gpu.chains_step(ch, 600)                                     # train on the chains' history
+    a0 = gpu.chains_read(ch, "accepts").copy()
+    gpu.chains_set_proposal(ch, None, gpu.PROPOSAL_UNIFORM)
+    gpu.chains_step(ch, 300)
+    a1 = gpu.chains_read(ch, "accepts").copy()
+    gpu.chains_set_proposal(ch, net, gpu.PROPOSAL_LEARNED, eps_mix=0.1)
+    gpu.chains_step(ch, 300)
+    a2 = gpu.chains_read(ch, "accepts")
+    acc_uniform = (a1 - a0).mean() / 300
+    acc_learned = (a2 - a1).mean() / 300
+    assert acc_learned > 1.5 * acc_uniform, (acc_learned, acc_uniform)

@@ -1,0 +1,101 @@
+"""GPU parity of the proposal network's tensor-core kernels.
+
+- bn_gemm_bf16 (tcgen05, TMEM accumulator) against a plain PyTorch fp32 matmul of the
+  same bf16 operands: FP32 accumulation in a different order, so rtol 1e-4.
+- forward, gradients and the Adam step against the FP64 oracle evaluated on the same
+  bf16 rounding points: differences come from FP32 accumulation and from bf16 roundings
+  of activations that land on the other side of a rounding boundary, so the bar is
+  1e-2 of the tensor's max-norm per element and 1e-3 on the relative Frobenius norm."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _weights(n, d, H, seed):
+    w = synth.mlp_init_weights(n, d, H, seed)
+    return w, omlp.MLPParams(*(np.asarray(w[k], np.float64) for k in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]))
+
+
+def _close(a, b, elem=1e-2, norm=1e-3):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = max(np.abs(b).max(), 1e-30)
+    assert np.abs(a - b).max() <= elem * scale, (np.abs(a - b).max(), scale)
+    assert np.linalg.norm(a - b) <= norm * max(np.linalg.norm(b), 1e-30) + 1e-30
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 512, 1920), (384, 256, 192), (256, 1792, 512),
+                                   (512, 512, 256)])
+def test_gemm_matches_torch(gpu, M, N, K):
+    import torch
+    g = torch.Generator().manual_seed(M * 7 + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    ref = A.float() @ B.float().T
+    out = gpu.gemm_bf16(A.cuda(), B.cuda()).cpu()
+    torch.testing.assert_close(out, ref, rtol=1e-4, atol=1e-3)
+
+
+def test_gemm_identity_and_zero_k(gpu):
+    import torch
+    A = torch.zeros(128, 64, dtype=torch.bfloat16)
+    A[:, :64] = torch.eye(128)[:, :64].to(torch.bfloat16)
+    B = torch.arange(128 * 64, dtype=torch.float32).reshape(128, 64).remainder(7).to(torch.bfloat16)
+    out = gpu.gemm_bf16(A.cuda(), B.cuda()).cpu()
+    # C[i][j] = sum_k A[i][k] B[j][k] = B[j][i] for i < 64
+    assert torch.equal(out[:64], B.float().T[:64])
+    assert torch.equal(out[64:], torch.zeros(64, 128))
+
+
+@pytest.mark.parametrize("n,d,H,B", [(6, 8, 128, 40), (60, 32, 512, 256)])
+def test_forward_matches_oracle(gpu, n, d, H, B):
+    w, prm = _weights(n, d, H, 5)
+    net = gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=B)
+    orders = synth.random_orders(n, B, 6)
+    logits = gpu.mlp_forward(net, orders)
+    ref = omlp.mlp_forward(prm, orders)["logits"]
+    _close(logits, ref)
+
+
+@pytest.mark.parametrize("n,d,H,B", [(6, 8, 128, 40), (60, 32, 512, 256)])
+def test_gradients_and_adam_match_oracle(gpu, n, d, H, B):
+    w, prm = _weights(n, d, H, 9)
+    net = gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=B, lr=1e-3)
+    rng = np.random.default_rng(n)
+    orders = synth.random_orders(n, B, 10)
+    pairs = rng.integers(0, n * (n - 1) // 2, B).astype(np.uint32)
+    alpha = rng.uniform(0, 1, B).astype(np.float32)
+    loss = gpu.mlp_loss_grad(net, orders, pairs, alpha)
+    ref_loss, ref_g = omlp.mlp_loss_grad(prm, orders, pairs.astype(np.int64), alpha.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    for name in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]:
+        _close(gpu.mlp_read(net, name, grad=True), ref_g[name], elem=2e-2, norm=1e-2)
+    gpu.mlp_adam_step(net)
+    st = {}
+    omlp.adam_step(prm, ref_g, st, lr=1e-3)
+    for name in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]:
+        before = np.asarray(w[name], np.float64)
+        upd = gpu.mlp_read(net, name) - before
+        ref_upd = getattr(prm, name) - before
+        # Adam's first step is lr * sign(g) wherever |g| >> eps: compare the updates where
+        # the oracle's gradient is clearly nonzero
+        gref = ref_g[name]
+        # where |g| approaches Adam's eps (1e-8) the first step lr g / (|g| + eps) is
+        # sensitive to the gradient's rounding; compare where |g| >> eps
+        big = np.abs(gref) > max(1e-3 * np.abs(gref).max(), 1e-6)
+        assert np.mean(np.sign(upd[big]) == np.sign(ref_upd[big])) > 0.98, name
+        agree = big & (np.sign(upd) == np.sign(ref_upd))
+        assert np.abs(upd[agree] - ref_upd[agree]).max(initial=0.0) <= 1e-5, name
+        assert np.abs(upd).max() <= 1e-3 * 1.001, name       # |first Adam step| <= lr
+
+
+def test_batch_above_capacity_rejected(gpu):
+    w, _ = _weights(6, 8, 128, 1)
+    net = gpu.mlp_create(6, w, hidden=128, d=8, batch_cap=100)
+    with pytest.raises(gpu.BNError) as e:
+        gpu.mlp_forward(net, synth.random_orders(6, 129, 1))
+    assert e.value.code == gpu.EINVAL
