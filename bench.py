@@ -4,9 +4,15 @@
 One step = one Metropolis-Hastings iteration of every chain: a swap proposal per chain,
 the order score of Eq. (6) of every proposed order (an exact full-order score; only the
 nodes between the swapped positions are re-scanned, the others keep their best sets),
-the MH test, best-graph and edge-count updates -- three kernels replayed from a CUDA
-graph.  Workload: 60 ternary nodes, in-degree <= 3, m = 1000 synthetic samples, k = 4
-(489,406 parent sets per node, 29.36 M FP64 entries, 235 MB), 256 chains.
+the MH test, best-graph and edge-count updates -- kernels replayed from a CUDA graph.
+Workload: 60 ternary nodes, in-degree <= 3, m = 1000 synthetic samples, k = 4 (489,406
+parent sets per node, 29.36 M FP64 entries, 235 MB), 256 chains.
+
+The headline runs the pruned scan (only table entries that no subset of their parent set
+matches or beats are tested -- the same results, see include/bn.h); the full-table scan
+is timed beside it with its own roofline.  Edge-posterior ESS/s of the plain uniform-swap
+sampler and of the learned-proposal sampler (trained on the plain sampler's history) are
+measured on the same table.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -45,6 +51,9 @@ def parse():
     ap.add_argument("--chains", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ess-steps", type=int, default=2000)
+    ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--no-ess", action="store_true")
     return ap.parse_args()
 
 
@@ -165,12 +174,53 @@ def run_reference(args):
     return 0
 
 
-def config_dict(chains):
+def config_dict(chains, scan="pruned"):
     return {"workload": f"{WORKLOAD}: 60 ternary nodes, random DAG in-degree<=3, m=1000 synthetic samples, "
                         f"k=4 (489,406 parent sets/node, 29.36M FP64 entries, 235 MB), {chains} chains, "
                         "uniform swap proposal",
-            "chains": chains, "n": 60, "k": 4, "m": 1000,
-            "l2": "inputs larger than L2 (235 MB table streamed per step)"}
+            "chains": chains, "n": 60, "k": 4, "m": 1000, "scan": scan,
+            "l2": "inputs larger than L2 (235 MB table; full-scan steps stream it every step)"}
+
+
+ALU_LANES_PER_SM = 64      # 32-bit logic / compare / min-max results per clock per SM
+SCAN_ALU_OPS = 3           # per (entry, item) test: 64-bit AND-NOT + zero test (2), min (1)
+
+
+def _timed(bn, torch, chains, steps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bn.chains_step(chains, steps, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _ess_run(bn, torch, table, chains, seed, pre_steps, steps, stream, net=None, train_steps=0):
+    """ESS of the edge indicators over `steps` recorded steps after `pre_steps` uniform
+    steps (and, for the learned sampler, `train_steps` of training on the history)."""
+    ch = bn.chains_create(table, chains, seed, burn_in=pre_steps + train_steps, record_every=1, record_cap=steps)
+    bn.chains_step(ch, pre_steps, stream=stream.cuda_stream)
+    t_train = 0.0
+    if net is not None:
+        bn.chains_set_proposal(ch, net, bn.PROPOSAL_TRAIN)
+        t_train = _timed(bn, torch, ch, train_steps, stream) / 1000.0
+        bn.chains_set_proposal(ch, net, bn.PROPOSAL_LEARNED, eps_mix=0.1)
+    elif train_steps:
+        bn.chains_step(ch, train_steps, stream=stream.cuda_stream)
+    a0 = bn.chains_read(ch, "accepts").copy()
+    sec = _timed(bn, torch, ch, steps, stream) / 1000.0
+    acc = float((bn.chains_read(ch, "accepts") - a0).mean() / steps)
+    f = bn.chains_read(ch, "edge_counts").sum(0) / (chains * steps)
+    ess = bn.chains_read(ch, "ess")
+    unc = (f >= 0.05) & (f <= 0.95) & ~np.isnan(ess)
+    med = float(np.median(ess[unc])) if unc.any() else None
+    mn = float(ess[unc].min()) if unc.any() else None
+    ch.free()
+    return dict(median_ess=med, min_ess=mn, uncertain_edges=int(unc.sum()), seconds=sec,
+                ess_per_s=(med / sec) if med else None, acceptance=acc, steps=steps, chains=chains,
+                train_seconds=t_train), f
 
 
 # ---------------------------------------------------------------------------------------
@@ -206,9 +256,9 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
     stream = torch.cuda.Stream(device=dev)
-    sp = stream.cuda_stream
     data, arity, k, R, _ = synth.workload(WORKLOAD)
     n = data.shape[1]
 
@@ -217,47 +267,81 @@ def main():
     t0 = time.perf_counter()
     table = bn.build_scores(data, arity, k, R=R)
     build_s = time.perf_counter() - t0
-    info = bn.table_info(table)
-    S = info["sets_per_node"]
+    S = bn.table_info(table)["sets_per_node"]
+    seed = 0xC0FFEE + 7919 * rank
 
-    chains = bn.chains_create(table, args.chains, seed=0xC0FFEE + 7919 * rank, burn_in=0)
     with torch.cuda.stream(stream):
-        bn.chains_step(chains, args.warmup, stream=sp)
+        # ---- full-table scan sampler ----------------------------------------------------
+        full = bn.chains_create(table, args.chains, seed=seed)
+        bn.chains_step(full, args.warmup, stream=stream.cuda_stream)
+        i0 = int(bn.chains_read(full, "items")[0])
+        ms_full = _timed(bn, torch, full, args.steps, stream)
+        items_full = int(bn.chains_read(full, "items")[0]) - i0
+        prof_steps = max(20, min(args.steps, 100))
+        i1 = int(bn.chains_read(full, "items")[0])
+        scan_ms_full, scan_l_full = bn.chains_step_profiled(full, prof_steps, stream=stream.cuda_stream)
+        items_prof = int(bn.chains_read(full, "items")[0]) - i1
+        full.free()
+
+        # ---- pruned scan sampler (headline) ----------------------------------------------
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bn.table_set_scan(table, bn.SCAN_PRUNED)
+        prune_s = time.perf_counter() - t0
+        survivors = bn.table_pruned(table)
+        chains = bn.chains_create(table, args.chains, seed=seed)
+        bn.chains_step(chains, args.warmup, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         barrier()
         clk = ClockSampler(local)
         clk.start()
         l0 = bn.kernel_launches()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        bn.chains_step(chains, args.steps, stream=sp)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        ms = _timed(bn, torch, chains, args.steps, stream)
         launches = bn.kernel_launches() - l0
         barrier()
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
-        # dominant kernel: the scan, timed launch by launch with events on this stream
-        prof_steps = max(20, min(args.steps, 200))
-        scan_ms, scan_launches = bn.chains_step_profiled(chains, prof_steps, stream=sp)
+        scan_ms_p, scan_l_p = bn.chains_step_profiled(chains, prof_steps, stream=stream.cuda_stream)
+        chains.free()
+
     t_max = ms
     if world > 1:
         tt = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    evals = world * args.chains * args.steps
-    value = evals / (t_max / 1000.0)
+    value = world * args.chains * args.steps / (t_max / 1000.0)
 
-    # end to end through the public C ABI with host buffers: table build from host data
-    # + a run of the sampler + results copied back, every call
-    e2e_steps = max(50, args.steps // 2)
+    # ---- edge-posterior ESS/s: plain vs learned proposal (same table, same chains) --------
+    ess = None
+    if not args.no_ess and rank == 0:
+        with torch.cuda.stream(stream):
+            pre = 300
+            plain, f_plain = _ess_run(bn, torch, table, args.chains, seed + 1, pre, args.ess_steps, stream,
+                                      train_steps=args.train_steps)
+            d, H = 32, 512
+            net = bn.mlp_create(n, synth.mlp_init_weights(n, d, H, seed), hidden=H, d=d, batch_cap=args.chains,
+                                lr=2e-3)
+            learned, f_learned = _ess_run(bn, torch, table, args.chains, seed + 2, pre, args.ess_steps, stream,
+                                          net=net, train_steps=args.train_steps)
+            # long plain run (8x) as the judge of the learned sampler's edge frequencies
+            long_ch = bn.chains_create(table, args.chains, seed + 3, burn_in=pre)
+            bn.chains_step(long_ch, pre + 8 * args.ess_steps, stream=stream.cuda_stream)
+            f_long = bn.chains_read(long_ch, "edge_counts").sum(0) / (args.chains * 8 * args.ess_steps)
+            long_ch.free()
+        ess = {"plain": plain, "learned": learned,
+               "max_abs_edge_freq_diff_learned_vs_long_plain": float(np.abs(f_learned - f_long).max()),
+               "max_abs_edge_freq_diff_plain_vs_long_plain": float(np.abs(f_plain - f_long).max()),
+               "long_plain_steps": 8 * args.ess_steps,
+               "learned_over_plain_ess_per_s": (learned["ess_per_s"] / plain["ess_per_s"])
+               if learned["ess_per_s"] and plain["ess_per_s"] else None}
+
+    # ---- end to end through the public C ABI with host buffers ----------------------------
+    e2e_steps = max(50, args.steps)
     e2e_calls = 2
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for c in range(e2e_calls):
         tb = bn.build_scores(data, arity, k, R=R)
+        bn.table_set_scan(tb, bn.SCAN_PRUNED)
         out = bn.mcmc_run(tb, args.chains, e2e_steps, seed=17 + c, burn_in=e2e_steps // 10)
         tb.free()
     e2e_s = (time.perf_counter() - t0) / e2e_calls
@@ -265,16 +349,22 @@ def main():
     h2d = data.nbytes + arity.nbytes + (R.nbytes if R is not None else 0)
     d2h = out["best_order"].nbytes + out["best_dag"].nbytes + 8 + out["edge_freq"].nbytes
 
-    line = None
     if rank == 0:
-        avg_scan = scan_ms / max(scan_launches, 1)
-        alg_bytes = 8 * n * S
-        achieved = alg_bytes / (avg_scan / 1000.0) / 1e9
-        roof = {"kernel": "k_scan", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": f"{peak_src} hbm_gbs",
-                "per_launch": {"algorithmic_bytes": alg_bytes, "avg_ms": avg_scan, "launches": scan_launches},
-                "share_of_step": (scan_ms / scan_launches) / (ms / args.steps)}
+        clock_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        avg_full = scan_ms_full / max(scan_l_full, 1)
+        tests = items_prof * S / max(scan_l_full, 1)                 # (entry, item) tests per launch
+        alu_peak = n_sm * ALU_LANES_PER_SM * clock_mhz * 1e6 / 1e9     # Gop/s
+        alu_ach = SCAN_ALU_OPS * tests / (avg_full / 1000.0) / 1e9
+        roof_full = {"kernel": "k_scan (full table)", "bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+                     "unit": "Gop/s", "frac": alu_ach / alu_peak, "traffic": None,
+                     "peak_source": f"derived: {n_sm} SMs x {ALU_LANES_PER_SM} int32 logic/min lanes x "
+                                    f"{clock_mhz:.0f} MHz (measured SM clock)",
+                     "per_launch": {"tests": tests, "alu_ops_per_test": SCAN_ALU_OPS, "avg_ms": avg_full,
+                                    "launches": scan_l_full,
+                                    "hbm_bytes_algorithmic": 12 * n * S,
+                                    "hbm_frac_of_measured": 12 * n * S / (avg_full / 1000.0) / 1e9 / hbm_peak},
+                     "share_of_step": avg_full / (ms_full / args.steps)}
+        avg_p = scan_ms_p / max(scan_l_p, 1)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, done, el = oracle_sample(args.cpu_seconds)
@@ -287,10 +377,17 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.chains),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "note": f"per call: bn_build_scores from host data + bn_mcmc_run of {e2e_steps} steps x "
-                            f"{args.chains} chains + results to host"},
+                    "note": f"per call: bn_build_scores from host data + pruning + bn_mcmc_run of {e2e_steps} "
+                            f"steps x {args.chains} chains + results to host"},
             "gpu_launches": int(launches),
-            "roofline": roof,
+            "roofline": roof_full,
+            "pruned_step": {"scan_avg_ms": avg_p, "scan_share_of_step": avg_p / (t_max / args.steps),
+                            "survivors_per_node_mean": float(survivors.mean()),
+                            "survivors_per_node_max": int(survivors.max()),
+                            "survivor_fraction": float(survivors.sum() / (n * S)), "prune_s": prune_s},
+            "full_scan": {"value": world * args.chains * args.steps / (ms_full / 1000.0),
+                          "ms_per_step": ms_full / args.steps, "items_per_step": items_full / args.steps},
+            "ess": ess,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "table_build_s": build_s,

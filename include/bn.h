@@ -131,6 +131,31 @@ int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* b
 int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
                             uint32_t* best_rank, double* order_score, void* stream);
 
+/* Scan mode of a table (used by bn_score_orders, bn_score_orders_noalloc and samplers
+ * whose next step is captured after the change):
+ *   BN_SCAN_FULL    every entry of a node's table is tested against every order (the
+ *                   default; Eq. (6) taken literally)
+ *   BN_SCAN_PRUNED  only entries that no proper subset of their parent set matches or
+ *                   beats are tested.  A dominated entry can never be chosen: whenever
+ *                   its set lies in a node's predecessors so does the subset, which has
+ *                   a score at least as high and a lower rank.  Results are identical.
+ *                   The surviving entries are kept in score order, so each order stops
+ *                   at its first consistent one.  The first switch builds them (k <= 7).
+ * Errors: BN_EINVAL, BN_ENOMEM, BN_EUNSUPPORTED, BN_ECUDA. */
+#define BN_SCAN_FULL   0
+#define BN_SCAN_PRUNED 1
+int bn_table_set_scan(bn_table* t, int mode, void* stream);
+/* surviving entries per node after pruning (n int64) */
+int bn_table_pruned(const bn_table* t, int64_t* survivors_per_node);
+
+/* Autotuner of the full-table scan: times every (shared-memory stage size in
+ * {512, 1024, 2048} entries) x (blocks per SM target in {1, 2, 4, 8, 16}) tiling on this
+ * table with synthetic work lists of max_items (node, order) items per node, and keeps
+ * the fastest for later scans of up to that many items (per 256-item group, up to 2048).
+ * chosen (3 int64, may be NULL): stage size, blocks per node, microseconds per launch.
+ * The table's scan mode is unchanged.  Errors: BN_EINVAL, BN_EUNSUPPORTED, BN_ECUDA. */
+int bn_table_autotune(bn_table* t, int max_items, void* stream, int64_t* chosen);
+
 /* Candidate-space mask of a rank and back (host-side helpers, no GPU needed).
  * mask bit c = candidate slot c.  Errors: BN_EINVAL if rank >= S(N,k) or the mask has
  * more than k bits or bits at or above N. */
@@ -202,6 +227,8 @@ int bn_chains_step_profiled(bn_chains* c, int64_t steps, void* stream, double* s
                                   edge-indicator series, bit r of [c][i][m] = edge m -> i
                                   in chain c's r-th recorded state                       */
 #define BN_OUT_RECORD_LEN   14 /* 1 int64: states recorded so far per chain              */
+#define BN_OUT_ITEMS        15 /* 1 int64: (node, chain) items re-scored so far (every
+                                  step re-scores the nodes between the swapped positions) */
 int bn_chains_read(const bn_chains* c, int what, void* out, int mem, void* stream);
 
 void bn_chains_free(bn_chains* c);
@@ -295,6 +322,13 @@ int bn_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, i
 /* ---------------------------------------------------------------------------------- */
 /* Misc                                                                                */
 /* ---------------------------------------------------------------------------------- */
+
+/* Failure-detection self test (the paper has no counterpart): one kernel waits, with the
+ * library's bounded-wait helpers, on an mbarrier no thread arrives at and on a device
+ * flag no one sets; each wait gives up after timeout_ns (<= 2 s) and records it in a
+ * status word.  Returns BN_ETIMEOUT when both waits ran out as intended (the context
+ * stays usable), BN_ECUDA otherwise. */
+int bn_selftest_timeout(int64_t timeout_ns, void* stream);
 
 const char* bn_last_error(void);     /* thread-local; "" when no error                 */
 const char* bn_version(void);

@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 MEM_HOST, MEM_DEVICE = 0, 1
 OUT = dict(orders=1, scores=2, ranks=3, best_orders=4, best_scores=5, best_ranks=6,
            edge_counts=7, accepts=8, trace_score=9, trace_accept=10, steps=11, ess=12, record=13,
-           record_len=14)
+           record_len=14, items=15)
 
 # names the ABI exports (include/bn.h); tests check the library against this list
 ABI = ["bn_build_scores", "bn_table_from_scores", "bn_table_info", "bn_table_scores",
@@ -96,6 +96,10 @@ def _load():
     _L.bn_mlp_free.restype = None
     _L.bn_gemm_bf16.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
     _L.bn_chains_set_proposal.argtypes = [_vp, _vp, C.c_int, C.c_double, _vp]
+    _L.bn_table_set_scan.argtypes = [_vp, C.c_int, _vp]
+    _L.bn_table_pruned.argtypes = [_vp, _vp]
+    _L.bn_table_autotune.argtypes = [_vp, C.c_int, _vp, _vp]
+    _L.bn_selftest_timeout.argtypes = [C.c_int64, _vp]
     return _L
 
 
@@ -262,6 +266,29 @@ def score_orders(t: Table, orders):
     return br, sc
 
 
+SCAN_FULL, SCAN_PRUNED = 0, 1
+
+
+def table_set_scan(t: Table, mode: int):
+    """Full-table scan or the scan over entries no subset dominates (bn_table_set_scan)."""
+    _check(lib().bn_table_set_scan(t.handle, mode, None))
+
+
+def table_autotune(t: Table, max_items: int):
+    """Time the full scan's tilings and keep the fastest -> (stage size, blocks per node,
+    microseconds per launch)."""
+    out = np.zeros(3, np.int64)
+    _check(lib().bn_table_autotune(t.handle, max_items, None, _ptr(out)))
+    return tuple(int(x) for x in out)
+
+
+def table_pruned(t: Table):
+    """Surviving entries per node after pruning."""
+    out = np.zeros(table_info(t)["n"], np.int64)
+    _check(lib().bn_table_pruned(t.handle, _ptr(out)))
+    return out
+
+
 def unrank(N, k, rank) -> int:
     m = C.c_uint64()
     _check(lib().bn_unrank(N, k, rank, C.byref(m)))
@@ -328,7 +355,7 @@ _OUT_SHAPES = {
     "best_ranks": (np.uint32, "cn"), "edge_counts": (np.uint32, "cnn"),
     "accepts": (np.int64, "c"), "trace_score": (np.float64, "ct"),
     "trace_accept": (np.uint8, "ct"), "steps": (np.int64, "1"), "ess": (np.float64, "nn"),
-    "record": (np.uint64, "cnnw"), "record_len": (np.int64, "1"),
+    "record": (np.uint64, "cnnw"), "record_len": (np.int64, "1"), "items": (np.int64, "1"),
 }
 
 

@@ -52,9 +52,55 @@ int sm_count()
     return v;
 }
 
+// A wait that can only run out: an mbarrier nobody arrives at, and a global flag nobody
+// sets, each waited on with the same bounded helpers the kernels use.
+__global__ void k_selftest_wait(const volatile uint32_t* flag, uint64_t timeout_ns, uint32_t* status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait_bounded(&bar, 0, timeout_ns)) atomicOr(status, STATUS_TIMEOUT);
+        const uint64_t t0 = global_timer_ns();
+        while (*flag == 0u) {
+            if (global_timer_ns() - t0 > timeout_ns) {
+                atomicOr(status, STATUS_TIMEOUT << 1);
+                break;
+            }
+        }
+    }
+}
+
 }  // namespace bn
 
 extern "C" {
+
+int bn_selftest_timeout(int64_t timeout_ns, void* stream)
+{
+    bn::t_err[0] = 0;
+    if (timeout_ns <= 0 || timeout_ns > 2000000000LL)
+        return bn::set_error(BN_EINVAL, "bn_selftest_timeout: timeout must be in (0, 2 s]");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* d = nullptr;
+    BN_CUDA(cudaMallocAsync((void**)&d, 8, s));
+    BN_CUDA(cudaMemsetAsync(d, 0, 8, s));
+    bn::k_selftest_wait<<<1, 32, 0, s>>>(d, (uint64_t)timeout_ns, d + 1);
+    cudaError_t le = cudaGetLastError();
+    uint32_t h = 0;
+    if (le == cudaSuccess) {
+        bn::count_launches(1);
+        le = cudaMemcpyAsync(&h, d + 1, 4, cudaMemcpyDeviceToHost, s);
+    }
+    cudaFreeAsync(d, s);
+    if (le != cudaSuccess) return bn::cuda_fail(le, "k_selftest_wait", __FILE__, __LINE__);
+    BN_CUDA(cudaStreamSynchronize(s));
+    if (h == (bn::STATUS_TIMEOUT | (bn::STATUS_TIMEOUT << 1)))
+        return bn::set_error(BN_ETIMEOUT, "bn_selftest_timeout: both bounded waits gave up as intended");
+    return bn::set_error(BN_ECUDA, "bn_selftest_timeout: unexpected status %u", h);
+}
 
 const char* bn_last_error(void) { return bn::t_err; }
 

@@ -58,6 +58,7 @@ struct ChainState {
     uint8_t* trace_accept;
     uint64_t* rec_bits;        // C*n*n*rec_words
     int64_t* rec_count;        // 1
+    int64_t* items_total;      // 1  (node, chain) items scanned so far
     // proposal (BN_PROPOSAL_*): learned draws and their log proposal probabilities
     int mode;
     int P;                     // n(n-1)/2
@@ -134,10 +135,58 @@ __global__ void k_init_state(ChainState S)
     }
 }
 
-// step 1: proposal and work lists
+// the swapped order and the work items of the positions a..b (their predecessor sets
+// changed), one warp per chain: lane l owns positions l and l + 32, prefix masks by a
+// warp OR-scan, the list appends in parallel
+__device__ __forceinline__ void swap_and_list(const ChainState& S, int c, int a, int b, int lane)
+{
+    const int n = S.n;
+    uint8_t* po = S.prop_order + (size_t)c * n;
+    const uint8_t* co = S.cur_order + (size_t)c * n;
+    int v[2];
+    uint64_t bit[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = lane + 32 * h;
+        v[h] = -1;
+        bit[h] = 0;
+        if (p < n) {
+            v[h] = (p == a) ? co[b] : (p == b) ? co[a] : co[p];
+            po[p] = (uint8_t)v[h];
+            bit[h] = 1ull << v[h];
+        }
+    }
+    // inclusive OR-scan over positions 0..31, then 32..63 on top of the first half's total
+    uint64_t s0 = bit[0], s1 = bit[1];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t t0 = __shfl_up_sync(0xffffffffu, s0, off);
+        const uint64_t t1 = __shfl_up_sync(0xffffffffu, s1, off);
+        if (lane >= off) { s0 |= t0; s1 |= t1; }
+    }
+    const uint64_t first_half = __shfl_sync(0xffffffffu, s0, 31);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = lane + 32 * h;
+        if (p < n && p >= a && p <= b) {
+            const uint64_t excl = (h == 0 ? s0 : (s1 | first_half)) & ~bit[h];   // nodes before position p
+            const uint32_t slot = atomicAdd(&S.list_count[v[h]], 1u);
+            S.list_pc[(size_t)v[h] * S.C + slot] = compress_pred(excl, v[h]);
+            S.list_best[(size_t)v[h] * S.C + slot] = SPOS_NONE;
+            S.slot_of[(size_t)c * n + v[h]] = slot;
+        }
+    }
+    if (lane == 0) {
+        S.prop_ab[2 * c] = (uint8_t)a;
+        S.prop_ab[2 * c + 1] = (uint8_t)b;
+    }
+}
+
+// step 1: proposal and work lists (one warp per chain)
 __global__ void k_propose(ChainState S)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= S.C) return;
     const int n = S.n;
     const int64_t t = *S.step;
@@ -145,25 +194,8 @@ __global__ void k_propose(ChainState S)
     const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
     int a, b;
     pair_decode(n, mulhi64(x.x[0], P), a, b);
-    const double u = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
-    uint8_t* po = S.prop_order + (size_t)c * n;
-    const uint8_t* co = S.cur_order + (size_t)c * n;
-    uint64_t prefix = 0;
-    for (int p = 0; p <= b; ++p) {
-        int v = (p == a) ? co[b] : (p == b) ? co[a] : co[p];
-        po[p] = (uint8_t)v;
-        if (p >= a) {
-            uint32_t slot = atomicAdd(&S.list_count[v], 1u);
-            S.list_pc[(size_t)v * S.C + slot] = compress_pred(prefix, v);
-            S.list_best[(size_t)v * S.C + slot] = SPOS_NONE;
-            S.slot_of[(size_t)c * n + v] = slot;
-        }
-        prefix |= 1ull << v;
-    }
-    for (int p = b + 1; p < n; ++p) po[p] = co[p];
-    S.prop_ab[2 * c] = (uint8_t)a;
-    S.prop_ab[2 * c + 1] = (uint8_t)b;
-    S.prop_u[c] = u;
+    swap_and_list(S, c, a, b, lane);
+    if (lane == 0) S.prop_u[c] = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
 }
 
 // step 3: combine, MH test, bookkeeping; the last block advances the step counter
@@ -261,7 +293,12 @@ __global__ void k_accept(ChainState S)
         __threadfence();
         const uint32_t ticket = atomicAdd(S.done, 1u);
         if (ticket == gridDim.x - 1) {
-            for (int i = 0; i < n; ++i) S.list_count[i] = 0;
+            int64_t items = 0;
+            for (int i = 0; i < n; ++i) {
+                items += S.list_count[i];
+                S.list_count[i] = 0;
+            }
+            *S.items_total += items;
             if (t >= S.burn_in && S.record_every > 0 && ((t - S.burn_in) % S.record_every) == 0 &&
                 (t - S.burn_in) / S.record_every < S.record_cap)
                 *S.rec_count = (t - S.burn_in) / S.record_every + 1;
@@ -309,30 +346,14 @@ __global__ void k_propose_learned(ChainState S)
         if (pair < 0) pair = j1 - 1;
     }
     pair = __shfl_sync(0xffffffffu, pair, owner);
-    if (lane != 0) return;
     int a, b;
     pair_decode(n, (uint64_t)pair, a, b);
-    const double um = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
-    uint8_t* po = S.prop_order + (size_t)c * n;
-    const uint8_t* co = S.cur_order + (size_t)c * n;
-    uint64_t prefix = 0;
-    for (int p = 0; p <= b; ++p) {
-        const int v = (p == a) ? co[b] : (p == b) ? co[a] : co[p];
-        po[p] = (uint8_t)v;
-        if (p >= a) {
-            const uint32_t slot = atomicAdd(&S.list_count[v], 1u);
-            S.list_pc[(size_t)v * S.C + slot] = compress_pred(prefix, v);
-            S.list_best[(size_t)v * S.C + slot] = SPOS_NONE;
-            S.slot_of[(size_t)c * n + v] = slot;
-        }
-        prefix |= 1ull << v;
+    swap_and_list(S, c, a, b, lane);
+    if (lane == 0) {
+        S.prop_u[c] = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
+        S.prop_pair[c] = (uint32_t)pair;
+        S.prop_lqf[c] = lq[pair];
     }
-    for (int p = b + 1; p < n; ++p) po[p] = co[p];
-    S.prop_ab[2 * c] = (uint8_t)a;
-    S.prop_ab[2 * c + 1] = (uint8_t)b;
-    S.prop_u[c] = um;
-    S.prop_pair[c] = (uint32_t)pair;
-    S.prop_lqf[c] = lq[pair];
 }
 
 // log q(. | order) of every chain from the network's logits (row stride ldl):
@@ -490,6 +511,7 @@ struct bn_chains {
     void* prop_block = nullptr;     // learned-proposal buffers (bn_chains_set_proposal)
     bn_mlp* mlp = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int exec_scan_mode = -1;        // table scan mode the graph was captured with
     int per_sweep = 3;              // kernel launches per step
     int64_t steps = 0;
     int dev = 0;
@@ -508,7 +530,7 @@ static int sweep_launch(bn_chains* ch, cudaStream_t s, cudaEvent_t ev0 = nullptr
         k_log_q<<<(S.C + 7) / 8, 256, 0, s>>>(ch->mlp->L, ch->mlp->Pp, S.C, S.P, S.eps_mix, S.prop_lq);
         BN_LAUNCH_CHECK("k_log_q");
     } else {
-        k_propose<<<(S.C + 127) / 128, 128, 0, s>>>(S);
+        k_propose<<<(S.C + 7) / 8, 256, 0, s>>>(S);
         BN_LAUNCH_CHECK("k_propose");
     }
     if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
@@ -568,7 +590,7 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     size_t o_edge = take(4 * Cn * n), o_prop_order = take(Cn), o_prop_ab = take(2 * C), o_prop_u = take(8 * C);
     size_t o_cnt = take(4 * (size_t)n), o_pc = take(8 * Cn), o_slot = take(4 * Cn);
     size_t o_best = take(4 * Cn);
-    size_t o_step = take(8), o_status = take(4), o_done = take(4), o_rec_count = take(8);
+    size_t o_step = take(8), o_status = take(4), o_done = take(4), o_rec_count = take(8), o_items = take(8);
     size_t o_ts = take(8 * (size_t)C * S.trace_cap), o_ta = take((size_t)C * S.trace_cap);
     size_t o_rec = take(8 * Cn * n * S.rec_words);
     size_t o_init = take(mem == BN_MEM_HOST && init_orders ? Cn : 0);
@@ -599,6 +621,7 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
     S.status = (uint32_t*)(B + o_status);
     S.done = (uint32_t*)(B + o_done);
     S.rec_count = (int64_t*)(B + o_rec_count);
+    S.items_total = (int64_t*)(B + o_items);
     S.trace_score = (double*)(B + o_ts);
     S.trace_accept = B + o_ta;
     S.rec_bits = (uint64_t*)(B + o_rec);
@@ -663,8 +686,13 @@ extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
             if (s) cudaStreamDestroy(s);
         }
     } own_guard{own};
+    if (ch->exec && ch->exec_scan_mode != ch->t->scan_mode) {
+        cudaGraphExecDestroy(ch->exec);
+        ch->exec = nullptr;
+    }
     if (!ch->exec) {
         cudaGraph_t g = nullptr;
+        ch->exec_scan_mode = ch->t->scan_mode;
         BN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         int rc = sweep_launch(ch, s);
         cudaError_t ce = cudaStreamEndCapture(s, &g);
@@ -748,6 +776,7 @@ extern "C" int bn_chains_read(const bn_chains* ch, int what, void* out, int mem,
         case BN_OUT_STEPS: src = S.step; bytes = 8; break;
         case BN_OUT_RECORD: src = S.rec_bits; bytes = 8 * Cn * S.n * S.rec_words; break;
         case BN_OUT_RECORD_LEN: src = S.rec_count; bytes = 8; break;
+        case BN_OUT_ITEMS: src = S.items_total; bytes = 8; break;
         case BN_OUT_ESS: {
             int64_t T = 0;
             BN_CUDA(cudaMemcpyAsync(&T, S.rec_count, 8, cudaMemcpyDeviceToHost, s));

@@ -23,10 +23,13 @@ namespace bn {
 
 static constexpr int SCAN_THREADS = 256;
 static constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-static constexpr int SCAN_SUB = 1024;      // entries per shared-memory stage
-static constexpr int SCAN_STAGES = 4;
-static constexpr size_t SCAN_SMEM =
-    (size_t)SCAN_STAGES * SCAN_SUB * (sizeof(uint32_t) + sizeof(uint64_t)) + 8 * SCAN_STAGES;
+// stage size (entries) and pipeline depth; 48 KB of shared memory for the 1024 and 512
+// variants, 72 KB for 2048
+template <int SUB>
+struct ScanCfg {
+    static constexpr int STAGES = SUB >= 2048 ? 3 : (SUB >= 1024 ? 4 : 8);
+    static constexpr size_t SMEM = (size_t)STAGES * SUB * (sizeof(uint32_t) + sizeof(uint64_t)) + 8 * STAGES;
+};
 
 struct ScanArgs {
     const uint32_t* spos;
@@ -41,12 +44,11 @@ struct ScanArgs {
     uint32_t* status;
 };
 
-ScanPlan plan_scan(const bn_table* t, int max_items)
+static ScanPlan plan_for(const bn_table* t, int groups, int64_t target, int sub)
 {
     ScanPlan p;
-    const int groups = std::max(1, (max_items + SCAN_THREADS - 1) / SCAN_THREADS);
+    p.sub = sub;
     const int64_t units = t->Sp / SUBQ;
-    const int64_t target = (int64_t)sm_count() * 4 * 2;     // two waves of four blocks per SM
     int64_t nchunk = (target + (int64_t)t->n * groups - 1) / ((int64_t)t->n * groups);
     nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, units));
     const int64_t chunk = round_up((t->Sp + nchunk - 1) / nchunk, SUBQ);
@@ -55,6 +57,20 @@ ScanPlan plan_scan(const bn_table* t, int max_items)
     return p;
 }
 
+ScanPlan plan_scan(const bn_table* t, int max_items)
+{
+    const int groups = std::max(1, (max_items + SCAN_THREADS - 1) / SCAN_THREADS);
+    if (groups <= 8 && t->tuned_sub[groups]) {
+        ScanPlan p;
+        p.sub = t->tuned_sub[groups];
+        p.nchunk = t->tuned_nchunk[groups];
+        p.chunk = t->tuned_chunk[groups];
+        return p;
+    }
+    return plan_for(t, groups, (int64_t)sm_count() * 4 * 2, 1024);   // two waves of four blocks per SM
+}
+
+template <int SCAN_SUB>
 __device__ __forceinline__ void scan_issue(const ScanArgs& A, int node, int64_t base, int64_t e1, uint32_t* s_sp,
                                            uint64_t* s_msk, uint64_t* bar, uint64_t pol_stream, uint64_t pol_keep)
 {
@@ -64,8 +80,10 @@ __device__ __forceinline__ void scan_issue(const ScanArgs& A, int node, int64_t 
     bulk_g2s(s_msk, A.pst + base, cnt * 8u, bar, pol_keep);
 }
 
+template <int SCAN_SUB>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
 {
+    constexpr int SCAN_STAGES = ScanCfg<SCAN_SUB>::STAGES;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* s_msk = (uint64_t*)smem;                                          // [STAGES][SUB]
     uint32_t* s_sp = (uint32_t*)(smem + sizeof(uint64_t) * SCAN_STAGES * SCAN_SUB);
@@ -101,7 +119,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < SCAN_STAGES && s < nsub; ++s)
-            scan_issue(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_sp + s * SCAN_SUB, s_msk + s * SCAN_SUB, &bar[s],
+            scan_issue<SCAN_SUB>(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_sp + s * SCAN_SUB, s_msk + s * SCAN_SUB, &bar[s],
                        pol_stream, pol_keep);
     }
 
@@ -128,7 +146,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
             const int64_t base = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
-            scan_issue(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st], pol_stream,
+            scan_issue<SCAN_SUB>(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st], pol_stream,
                        pol_keep);
         }
     }
@@ -148,6 +166,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
 int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_count, const uint64_t* list_pc,
                 uint32_t* list_best, int cap, uint32_t* status, cudaStream_t s)
 {
+    if (t->scan_mode == BN_SCAN_PRUNED) return launch_scan_pruned(t, list_count, list_pc, list_best, cap, s);
     ScanArgs A;
     A.spos = t->spos;
     A.pst = t->pst;
@@ -159,16 +178,36 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
     A.list_best = list_best;
     A.cap = cap;
     A.status = status;
-    static bool attr_set[64] = {false};
+    static bool attr_set[64][3] = {{false}};
     const int d = device_id();
-    if (d < 64 && !attr_set[d]) {
-        BN_CUDA(cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCAN_SMEM));
-        attr_set[d] = true;
+    const int v = pl.sub >= 2048 ? 2 : (pl.sub >= 1024 ? 1 : 0);
+    if (d < 64 && !attr_set[d][v]) {
+        if (v == 2) BN_CUDA(cudaFuncSetAttribute(k_scan<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<2048>::SMEM));
+        if (v == 1) BN_CUDA(cudaFuncSetAttribute(k_scan<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<1024>::SMEM));
+        if (v == 0) BN_CUDA(cudaFuncSetAttribute(k_scan<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<512>::SMEM));
+        attr_set[d][v] = true;
     }
     dim3 grid((unsigned)(t->n * pl.nchunk), (unsigned)((cap + SCAN_THREADS - 1) / SCAN_THREADS));
-    k_scan<<<grid, SCAN_THREADS, SCAN_SMEM, s>>>(A);
+    if (v == 2) k_scan<2048><<<grid, SCAN_THREADS, ScanCfg<2048>::SMEM, s>>>(A);
+    else if (v == 1) k_scan<1024><<<grid, SCAN_THREADS, ScanCfg<1024>::SMEM, s>>>(A);
+    else k_scan<512><<<grid, SCAN_THREADS, ScanCfg<512>::SMEM, s>>>(A);
     BN_LAUNCH_CHECK("k_scan");
     return BN_OK;
+}
+
+// synthetic work lists for tuning: every node holds `items` items with pseudo-random
+// predecessor masks (a fixed integer hash of (node, item))
+__global__ void k_tune_lists(int n, int items, uint64_t* list_pc, uint32_t* list_best, uint32_t* list_count)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) list_count[idx] = (uint32_t)items;
+    if (idx >= n * items) return;
+    uint64_t h = (uint64_t)idx * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 32;
+    list_pc[idx] = h;
+    list_best[idx] = SPOS_NONE;
 }
 
 // a5: candidate-space predecessor masks, written straight into the node-major work
@@ -304,5 +343,84 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
     BN_CUDA(cudaStreamSynchronize(s));
     if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_score_orders: an order is not a permutation of 0..n-1");
     if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_score_orders: a bounded device wait expired");
+    return BN_OK;
+}
+
+extern "C" int bn_table_autotune(bn_table* t, int max_items, void* stream, int64_t* chosen)
+{
+    set_error(BN_OK, "");
+    if (!t || max_items < 1) return set_error(BN_EINVAL, "bn_table_autotune: bad arguments");
+    const int groups = std::max(1, (max_items + SCAN_THREADS - 1) / SCAN_THREADS);
+    if (groups > 8) return set_error(BN_EUNSUPPORTED, "bn_table_autotune: at most 2048 items");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = t->n, items = std::min(max_items, groups * SCAN_THREADS);
+    uint8_t* blk = nullptr;
+    const size_t o_pc = 0, o_best = (size_t)round_up(8 * (int64_t)n * items, 256),
+                 o_cnt = o_best + (size_t)round_up(4 * (int64_t)n * items, 256), o_st = o_cnt + 256;
+    BN_CUDA(cudaMallocAsync((void**)&blk, o_st + 256, s));
+    struct Free {
+        uint8_t* p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{blk, s};
+    uint64_t* pc = (uint64_t*)(blk + o_pc);
+    uint32_t* best = (uint32_t*)(blk + o_best);
+    uint32_t* cnt = (uint32_t*)(blk + o_cnt);
+    uint32_t* st = (uint32_t*)(blk + o_st);
+    BN_CUDA(cudaMemsetAsync(st, 0, 4, s));
+    cudaEvent_t e0, e1;
+    BN_CUDA(cudaEventCreate(&e0));
+    BN_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev()
+        {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{e0, e1};
+    const int saved_mode = t->scan_mode;
+    t->scan_mode = BN_SCAN_FULL;
+    float best_ms = 1e30f;
+    ScanPlan best_pl = plan_for(t, groups, (int64_t)sm_count() * 8, 1024);
+    const int subs[3] = {512, 1024, 2048};
+    const int per_sm[5] = {1, 2, 4, 8, 16};
+    int rc = BN_OK;
+    for (int si = 0; si < 3 && !rc; ++si) {
+        for (int bi = 0; bi < 5 && !rc; ++bi) {
+            const ScanPlan pl = plan_for(t, groups, (int64_t)sm_count() * per_sm[bi], subs[si]);
+            float tot = 0.f;
+            for (int rep = 0; rep < 4 && !rc; ++rep) {
+                k_tune_lists<<<(n * items + 255) / 256, 256, 0, s>>>(n, items, pc, best, cnt);
+                if (cudaGetLastError() != cudaSuccess) { rc = set_error(BN_ECUDA, "k_tune_lists"); break; }
+                count_launches(1);
+                if (cudaEventRecord(e0, s) != cudaSuccess) { rc = set_error(BN_ECUDA, "event"); break; }
+                rc = launch_scan(t, pl, cnt, pc, best, items, st, s);
+                if (rc) break;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = set_error(BN_ECUDA, "event sync");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;          // first launch warms up
+            }
+            if (!rc && tot < best_ms) { best_ms = tot; best_pl = pl; }
+        }
+    }
+    t->scan_mode = saved_mode;
+    if (rc) return rc;
+    t->tuned_sub[groups] = best_pl.sub;
+    t->tuned_nchunk[groups] = best_pl.nchunk;
+    t->tuned_chunk[groups] = best_pl.chunk;
+    if (chosen) {
+        chosen[0] = best_pl.sub;
+        chosen[1] = best_pl.nchunk;
+        chosen[2] = (int64_t)(1000.0f * best_ms / 3.0f);   // microseconds per launch
+    }
+    uint32_t hs = 0;
+    BN_CUDA(cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    if (hs & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_table_autotune: a bounded device wait expired");
     return BN_OK;
 }

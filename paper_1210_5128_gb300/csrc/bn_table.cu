@@ -642,5 +642,6 @@ extern "C" void bn_table_free(bn_table* t)
     cudaFree(t->pst);
     cudaFree(t->spos);
     cudaFree(t->srank);
+    cudaFree(t->alive_block);
     delete t;
 }

@@ -14,6 +14,22 @@ struct bn_table {
                                // ordered by score descending, rank ascending (padding: ~0)
     uint32_t* srank = nullptr; // [n][Sp] inverse of spos: rank at sorted position p
     size_t bytes = 0;
+    int scan_mode = 0;         // BN_SCAN_FULL or BN_SCAN_PRUNED
+    // entries not dominated by a proper subset, per node in sorted-position order
+    // (bn_prune.cu): candidate masks and sorted positions, node offsets and counts
+    uint64_t* amask = nullptr;
+    uint32_t* aspos = nullptr;
+    uint32_t* aoff = nullptr;
+    uint32_t* acnt = nullptr;
+    int64_t alive_total = 0;
+    uint32_t alive_max = 0;
+    int alive_chunks = 1;
+    void* alive_block = nullptr;
+    // full-scan tiling chosen by bn_table_autotune, per number of 256-item groups (1..8);
+    // tuned_sub == 0: not tuned
+    int tuned_sub[9] = {0};
+    int tuned_nchunk[9] = {0};
+    int64_t tuned_chunk[9] = {0};
 };
 
 namespace bn {
@@ -21,9 +37,15 @@ namespace bn {
 // Sorted positions and their inverse for every node (bn_sort.cu).
 int rank_entries(bn_table* t, cudaStream_t s);
 
+// Dominance pruning and the scan over the surviving entries (bn_prune.cu).
+int prune_table(bn_table* t, cudaStream_t s);
+int launch_scan_pruned(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc, uint32_t* list_best,
+                       int cap, cudaStream_t s);
+
 struct ScanPlan {
     int nchunk;        // blocks per node along the table
     int64_t chunk;     // entries per block (multiple of SUBQ)
+    int sub = 1024;    // entries per shared-memory stage (512, 1024 or 2048)
 };
 ScanPlan plan_scan(const bn_table* t, int max_items);
 

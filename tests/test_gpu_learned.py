@@ -47,15 +47,17 @@ def test_learned_proposal_keeps_the_posterior_n6(gpu):
     gpu.chains_step(ch, steps)
     f = gpu.chains_read(ch, "edge_counts").sum(0) / (C * (steps - burn))
     assert np.abs(f - exact).max() < 0.02, np.abs(f - exact).max()
-    # the proposal really was far from uniform: the learned chains accept at a different
-    # rate than uniform ones on the same table
+    # the proposal really was far from uniform: its pair probabilities span more than a
+    # factor of 5 on the chains' final orders
+    logits = gpu.mlp_forward(net, gpu.chains_read(ch, "orders"))
+    q = 0.8 * np.exp(logits - logits.max(1, keepdims=True))
+    q = q / (q.sum(1, keepdims=True) / 0.8) + 0.2 / logits.shape[1]
+    assert (q.max(1) / q.min(1)).min() > 5.0
+    # the uniform sampler agrees with the same posterior
     u = gpu.chains_create(t, C, 99, burn_in=burn)
     gpu.chains_step(u, steps)
     fu = gpu.chains_read(u, "edge_counts").sum(0) / (C * (steps - burn))
     assert np.abs(fu - exact).max() < 0.02
-    acc_l = gpu.chains_read(ch, "accepts").mean() / steps
-    acc_u = gpu.chains_read(u, "accepts").mean() / steps
-    assert abs(acc_l - acc_u) > 0.01, (acc_l, acc_u)
 
 
 def test_training_on_history_raises_acceptance_n20(gpu):

@@ -1,0 +1,103 @@
+"""The pruned scan (BN_SCAN_PRUNED) must give exactly the full scan's results: the same
+ranks bit for bit and the same scores, in bn_score_orders and in the sampler; and the set
+of surviving entries must be the one an independent dominance computation finds."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _survivors_python(T, n, k):
+    """Entries whose score beats every proper subset's (a separate restatement)."""
+    S = T.shape[1]
+    sets = [tuple(oracle.unrank(n - 1, k, r)) for r in range(S)]
+    index = {s: r for r, s in enumerate(sets)}
+    counts = []
+    for i in range(n):
+        best_le = np.empty(S)
+        alive = 0
+        for r, st in enumerate(sets):
+            sub = max((best_le[index[st[:t] + st[t + 1:]]] for t in range(len(st))), default=-np.inf)
+            best_le[r] = max(T[i, r], sub)
+            alive += T[i, r] > sub
+        counts.append(alive)
+    return np.array(counts)
+
+
+@pytest.mark.parametrize("name", ["n6_k2_m100", "n20_k4_m1000"])
+def test_survivors_match_python_dominance(gpu, name):
+    data, arity, k, R, _ = synth.workload(name)
+    n = data.shape[1]
+    t = gpu.build_scores(data, arity, k, R=R)
+    T = gpu.table_scores(t)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    assert np.array_equal(gpu.table_pruned(t), _survivors_python(T, n, k))
+
+
+@pytest.mark.parametrize("name,B", [("n6_k2_m100", 100), ("n20_k4_m1000", 300), ("n40_k4_m2000", 512),
+                                    ("n60_k4_m1000", 256)])
+def test_pruned_equals_full(gpu, name, B):
+    data, arity, k, R, _ = synth.workload(name)
+    n = data.shape[1]
+    t = gpu.build_scores(data, arity, k, R=R)
+    orders = synth.random_orders(n, B, 21)
+    br_f, sc_f = gpu.score_orders(t, orders)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    br_p, sc_p = gpu.score_orders(t, orders)
+    assert np.array_equal(br_f, br_p)
+    assert np.array_equal(sc_f, sc_p)
+    surv = gpu.table_pruned(t)
+    assert (surv >= 1).all() and surv.sum() < t.info()["sets_per_node"] * n
+
+
+def test_pruned_all_720_orders_vs_oracle(gpu):
+    data, arity, k, R, _ = synth.workload("n6_k2_m100", 1)
+    tab = oracle.build_table(data, arity, k)
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    orders = np.array(list(itertools.permutations(range(6))), np.uint8)
+    br, sc = gpu.score_orders(t, orders)
+    for b, o in enumerate(orders):
+        s, r = oracle.order_score(tab, k, o)
+        assert np.array_equal(br[b], r) and sc[b] == s
+
+
+def test_pruned_ties(gpu):
+    # every entry equal: everything but the empty set is dominated
+    n, k = 8, 3
+    tab = np.zeros((n, oracle.num_sets(n - 1, k)))
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    assert (gpu.table_pruned(t) == 1).all()
+    br, sc = gpu.score_orders(t, synth.random_orders(n, 50, 2))
+    assert (br == 0).all() and (sc == 0).all()
+
+
+def test_pruned_sampler_trajectories_vs_oracle(gpu):
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    tab = oracle.build_table(data, arity, k, R=R)
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    ch = gpu.chains_create(t, 8, 31, burn_in=50, trace_cap=300)
+    gpu.chains_step(ch, 300)
+    ref = oracle.mcmc_run(tab, k, 8, 300, seed=31, burn_in=50, trace=True)
+    assert np.array_equal(gpu.chains_read(ch, "trace_score"), ref["trace_score"])
+    assert np.array_equal(gpu.chains_read(ch, "edge_counts").astype(np.uint64), ref["edge_counts"])
+
+
+def test_switching_mode_recaptures_the_step(gpu):
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    a = gpu.chains_create(t, 16, 8, trace_cap=200)
+    gpu.chains_step(a, 100)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    gpu.chains_step(a, 100)
+    gpu.table_set_scan(t, gpu.SCAN_FULL)
+    b = gpu.chains_create(t, 16, 8, trace_cap=200)
+    gpu.chains_step(b, 200)
+    assert np.array_equal(gpu.chains_read(a, "trace_score"), gpu.chains_read(b, "trace_score"))

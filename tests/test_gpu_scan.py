@@ -105,6 +105,17 @@ def test_empty_batch_and_bad_orders(gpu):
         gpu.score_orders(t, bad)
 
 
+def test_autotuned_tiling_gives_identical_results(gpu):
+    data, arity, k, R, _ = synth.workload("n40_k4_m2000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    orders = synth.random_orders(40, 256, 12)
+    br0, sc0 = gpu.score_orders(t, orders)
+    sub, nchunk, us = gpu.table_autotune(t, 256)
+    assert sub in (512, 1024, 2048) and nchunk >= 1 and us > 0
+    br1, sc1 = gpu.score_orders(t, orders)
+    assert np.array_equal(br0, br1) and np.array_equal(sc0, sc1)
+
+
 @pytest.mark.parametrize("name,B", [("n40_k4_m2000", 512), ("n60_k4_m1000", 256)])
 def test_full_size_sampled_orders(gpu, name, B):
     """The full-size table built on the GPU, scored in the bench's batch shape; a seeded
