@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--chains", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ess-steps", type=int, default=2000)
+    ap.add_argument("--iters-per-step", type=int, default=1000,
+                    help="MH iterations of every chain in one timed step")
+    ap.add_argument("--ess-steps", type=int, default=20000)
+    ap.add_argument("--ess-thin", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-ess", action="store_true")
     return ap.parse_args()
@@ -76,7 +79,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -197,10 +200,12 @@ def _timed(bn, torch, chains, steps, stream):
     return e0.elapsed_time(e1)
 
 
-def _ess_run(bn, torch, table, chains, seed, pre_steps, steps, stream, net=None, train_steps=0):
-    """ESS of the edge indicators over `steps` recorded steps after `pre_steps` uniform
-    steps (and, for the learned sampler, `train_steps` of training on the history)."""
-    ch = bn.chains_create(table, chains, seed, burn_in=pre_steps + train_steps, record_every=1, record_cap=steps)
+def _ess_run(bn, torch, table, chains, seed, pre_steps, steps, stream, net=None, train_steps=0, thin=1):
+    """ESS of the edge indicators over `steps` steps (every `thin`-th state recorded)
+    after `pre_steps` uniform steps (and, for the learned sampler, `train_steps` of
+    training on the history)."""
+    ch = bn.chains_create(table, chains, seed, burn_in=pre_steps + train_steps, record_every=thin,
+                          record_cap=(steps + thin - 1) // thin)
     bn.chains_step(ch, pre_steps, stream=stream.cuda_stream)
     t_train = 0.0
     if net is not None:
@@ -289,18 +294,20 @@ def main():
         bn.table_set_scan(table, bn.SCAN_PRUNED)
         prune_s = time.perf_counter() - t0
         survivors = bn.table_pruned(table)
+        ips = args.iters_per_step
         chains = bn.chains_create(table, args.chains, seed=seed)
-        bn.chains_step(chains, args.warmup, stream=stream.cuda_stream)
+        bn.chains_step(chains, args.warmup * ips, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         barrier()
         clk = ClockSampler(local)
         clk.start()
         l0 = bn.kernel_launches()
-        ms = _timed(bn, torch, chains, args.steps, stream)
+        ms = _timed(bn, torch, chains, args.steps * ips, stream)
         launches = bn.kernel_launches() - l0
         barrier()
         clocks = clk.stop()
-        scan_ms_p, scan_l_p = bn.chains_step_profiled(chains, prof_steps, stream=stream.cuda_stream)
+        # the fused sampler kernel, launch by launch (256 iterations per launch)
+        fused_ms, fused_l = bn.chains_step_profiled(chains, max(ips, 256) * 4, stream=stream.cuda_stream)
         chains.free()
 
     t_max = ms
@@ -308,7 +315,7 @@ def main():
         tt = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    value = world * args.chains * args.steps / (t_max / 1000.0)
+    value = world * args.chains * args.steps * ips / (t_max / 1000.0)
 
     # ---- edge-posterior ESS/s: plain vs learned proposal (same table, same chains) --------
     ess = None
@@ -316,12 +323,12 @@ def main():
         with torch.cuda.stream(stream):
             pre = 300
             plain, f_plain = _ess_run(bn, torch, table, args.chains, seed + 1, pre, args.ess_steps, stream,
-                                      train_steps=args.train_steps)
+                                      train_steps=args.train_steps, thin=args.ess_thin)
             d, H = 32, 512
             net = bn.mlp_create(n, synth.mlp_init_weights(n, d, H, seed), hidden=H, d=d, batch_cap=args.chains,
                                 lr=2e-3)
             learned, f_learned = _ess_run(bn, torch, table, args.chains, seed + 2, pre, args.ess_steps, stream,
-                                          net=net, train_steps=args.train_steps)
+                                          net=net, train_steps=args.train_steps, thin=args.ess_thin)
             # long plain run (8x) as the judge of the learned sampler's edge frequencies
             long_ch = bn.chains_create(table, args.chains, seed + 3, burn_in=pre)
             bn.chains_step(long_ch, pre + 8 * args.ess_steps, stream=stream.cuda_stream)
@@ -335,7 +342,7 @@ def main():
                if learned["ess_per_s"] and plain["ess_per_s"] else None}
 
     # ---- end to end through the public C ABI with host buffers ----------------------------
-    e2e_steps = max(50, args.steps)
+    e2e_steps = max(50, args.steps) * args.iters_per_step
     e2e_calls = 2
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -364,7 +371,7 @@ def main():
                                     "hbm_bytes_algorithmic": 12 * n * S,
                                     "hbm_frac_of_measured": 12 * n * S / (avg_full / 1000.0) / 1e9 / hbm_peak},
                      "share_of_step": avg_full / (ms_full / args.steps)}
-        avg_p = scan_ms_p / max(scan_l_p, 1)
+        avg_fused = fused_ms / max(fused_l, 1)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, done, el = oracle_sample(args.cpu_seconds)
@@ -375,13 +382,16 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(args.chains),
+            "config": dict(config_dict(args.chains), iters_per_step=args.iters_per_step,
+                           step=f"{args.iters_per_step} MH iterations of every chain"),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "note": f"per call: bn_build_scores from host data + pruning + bn_mcmc_run of {e2e_steps} "
                             f"steps x {args.chains} chains + results to host"},
             "gpu_launches": int(launches),
             "roofline": roof_full,
-            "pruned_step": {"scan_avg_ms": avg_p, "scan_share_of_step": avg_p / (t_max / args.steps),
+            "pruned_step": {"kernel": "k_chain_fused (256 MH iterations per launch, one warp per chain)",
+                            "avg_ms_per_launch": avg_fused, "launches": fused_l,
+                            "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
                             "survivors_per_node_mean": float(survivors.mean()),
                             "survivors_per_node_max": int(survivors.max()),
                             "survivor_fraction": float(survivors.sum() / (n * S)), "prune_s": prune_s},

@@ -243,6 +243,21 @@ int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
                 uint8_t* best_order, uint8_t* best_dag, double* best_score,
                 double* edge_freq, void* stream);
 
+/* Batches of networks of uneven size (the paper samples one network at a time): count
+ * networks, each with its own table and chain parameters.  bn_batch_step advances every
+ * network by `steps` MH steps; the networks whose chains use the uniform proposal on a
+ * pruned table (BN_SCAN_PRUNED) advance together in one fused launch per 256 steps (one
+ * warp per chain of every network), the others through their own per-network steps.
+ * Results equal stepping each network's chains alone.  bn_batch_chains gives network
+ * i's chains (for bn_chains_read / bn_chains_set_proposal); they are freed with the
+ * batch.  The tables must outlive the batch. */
+typedef struct bn_batch bn_batch;
+int bn_batch_create(int count, const bn_table* const* tables, const bn_mcmc_params* params,
+                    void* stream, bn_batch** out);
+int bn_batch_chains(bn_batch* b, int i, bn_chains** out);
+int bn_batch_step(bn_batch* b, int64_t steps, void* stream);
+void bn_batch_free(bn_batch* b);
+
 /* ---------------------------------------------------------------------------------- */
 /* Learned swap proposal                                                               */
 /* ---------------------------------------------------------------------------------- */

@@ -99,6 +99,11 @@ def _load():
     _L.bn_table_set_scan.argtypes = [_vp, C.c_int, _vp]
     _L.bn_table_pruned.argtypes = [_vp, _vp]
     _L.bn_table_autotune.argtypes = [_vp, C.c_int, _vp, _vp]
+    _L.bn_batch_create.argtypes = [C.c_int, _vp, _vp, _vp, C.POINTER(_vp)]
+    _L.bn_batch_chains.argtypes = [_vp, C.c_int, C.POINTER(_vp)]
+    _L.bn_batch_step.argtypes = [_vp, C.c_int64, _vp]
+    _L.bn_batch_free.argtypes = [_vp]
+    _L.bn_batch_free.restype = None
     _L.bn_selftest_timeout.argtypes = [C.c_int64, _vp]
     return _L
 
@@ -444,6 +449,55 @@ def mlp_read(m: MLP, name: str, grad=False):
     what = MLP_TENSORS.index(name) + (7 if grad else 0)
     _check(lib().bn_mlp_read(m.handle, what, _ptr(out), MEM_HOST, None))
     return out
+
+
+class _BorrowedChains(Chains):
+    """Chains owned by a batch (freed with it)."""
+
+    def free(self):
+        self._h = None
+
+
+class Batch:
+    """Owns a bn_batch*: many networks' chains stepped together (bn_batch_*)."""
+
+    def __init__(self, handle, tables, chains_list):
+        self._h, self.tables, self._chains = handle, tables, chains_list
+
+    def chains(self, i) -> Chains:
+        return self._chains[i]
+
+    def step(self, steps, stream=None):
+        _check(lib().bn_batch_step(self._h, steps, stream))
+
+    def free(self):
+        if self._h:
+            lib().bn_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def batch_create(tables, chains, seeds, burn_in=0, record_every=0, record_cap=0, trace_cap=0) -> Batch:
+    """One chain set per table; `chains` and `seeds` are ints or per-network lists."""
+    cnt = len(tables)
+    chains = chains if hasattr(chains, "__len__") else [chains] * cnt
+    seeds = seeds if hasattr(seeds, "__len__") else [seeds + i for i in range(cnt)]
+    ps = (MCMCParams * cnt)(*[MCMCParams(int(chains[i]), burn_in, int(seeds[i]), 0, record_every, record_cap,
+                                         1 if trace_cap else 0, trace_cap) for i in range(cnt)])
+    hs = (C.c_void_p * cnt)(*[t.handle for t in tables])
+    h = _vp()
+    _check(lib().bn_batch_create(cnt, hs, ps, None, C.byref(h)))
+    lst = []
+    for i in range(cnt):
+        ch = _vp()
+        _check(lib().bn_batch_chains(h, i, C.byref(ch)))
+        lst.append(_BorrowedChains(ch, tables[i], table_info(tables[i])["n"], ps[i]))
+    return Batch(h, tables, lst)
 
 
 PROPOSAL_UNIFORM, PROPOSAL_LEARNED, PROPOSAL_TRAIN = 0, 1, 2

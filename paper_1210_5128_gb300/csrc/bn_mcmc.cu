@@ -68,6 +68,7 @@ struct ChainState {
     uint32_t* prop_pair;       // C
     float* prop_lqf;           // C  log q(pair | current)
     float* delta;              // C  s' - s of the last step (training target)
+    uint8_t* changed;          // C  1 if the last proposal changed some node's parent set
     uint8_t* train_orders;     // C*n  pre-step orders of the last step
     uint32_t* train_pairs;     // C
     float* train_alpha;        // C
@@ -211,6 +212,7 @@ __global__ void k_accept(ChainState S)
     if (c < S.C) {
         const int a = S.prop_ab[2 * c], b = S.prop_ab[2 * c + 1];
         const uint8_t* po = S.prop_order + (size_t)c * n;
+        bool moved = false;
         for (int p = lane; p < n; p += 32) {
             const int v = po[p];
             int64_t bk;
@@ -218,6 +220,7 @@ __global__ void k_accept(ChainState S)
             if (p >= a && p <= b) {
                 const uint32_t slot = S.slot_of[(size_t)c * n + v];
                 item_result(S, v, S.list_best[(size_t)v * S.C + slot], bk, br);
+                moved |= br != S.cur_rank[(size_t)c * n + v];
             } else {
                 bk = S.cur_key[(size_t)c * n + v];
                 br = S.cur_rank[(size_t)c * n + v];
@@ -225,6 +228,8 @@ __global__ void k_accept(ChainState S)
             s_key[warp][v] = bk;
             s_rank[warp][v] = br;
         }
+        moved = __any_sync(0xffffffffu, moved);
+        if (S.changed && lane == 0) S.changed[c] = moved ? 1 : 0;
         __syncwarp();
         if (lane == 0) {
             double s2 = 0.0;
@@ -309,6 +314,298 @@ __global__ void k_accept(ChainState S)
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Fused steps for the pruned table and the uniform proposal: one warp per chain runs
+// `iters` MH steps without leaving the kernel (chains are independent).  Per step: the
+// Philox draw, the swapped span's nodes re-scored by their lanes (each walks its node's
+// survivors in score order to the first consistent one), the FP64 order score summed in
+// ascending node id by lane 0, the MH test, the best graph.  Edge counts are accumulated
+// by dwell time: when a node's parent set changes at step t, its old set is credited
+// with the post-burn-in steps it was held; everything is flushed at the end of the
+// launch, so the counts equal per-step counting exactly.
+// ---------------------------------------------------------------------------------
+struct FusedArgs {
+    const uint64_t* amask;
+    const uint32_t* aspos;
+    const uint32_t* aoff;
+    const uint32_t* acnt;
+    int64_t t0;          // first step of this launch
+    int iters;
+    int staged;          // 1: the network's survivors fit the warp's shared-memory cache
+    int cap;             // survivors per warp cache (shared-memory layout of the launch)
+};
+
+// per-warp shared-memory cache of a network's survivors: candidate mask, rank and key of
+// every survivor, and the node offsets
+__host__ __device__ constexpr size_t surv_cache_bytes(int cap)
+{
+    return (size_t)cap * (8 + 8 + 4) + 4 * (MAXN + 1);
+}
+static constexpr int SURV_CAP_MAX = 2400;
+
+static constexpr int FUSED_WARPS = 2;
+
+__device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, uint32_t rank, int64_t from, int64_t to)
+{
+    const int64_t lo = max(from, S.burn_in);
+    if (to <= lo) return;
+    const uint32_t d = (uint32_t)(to - lo);
+    uint64_t m = S.pst[rank];
+    uint32_t* E = S.edge + ((size_t)c * S.n + v) * S.n;
+    while (m) {
+        const int slot = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        E[slot + (slot >= v ? 1 : 0)] += d;
+    }
+}
+
+struct FusedSmem {
+    uint8_t ord[MAXN];
+    uint32_t rank[MAXN];
+    int64_t key[MAXN];
+    int64_t nkey[MAXN];
+    int64_t since[MAXN];
+};
+
+__device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
+                                                 FusedSmem& W, uint8_t* cache)
+{
+    const int n = S.n;
+    const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
+    uint64_t* c_mask = (uint64_t*)cache;
+    int64_t* c_key = (int64_t*)(cache + 8 * (size_t)F.cap);
+    uint32_t* c_rank = (uint32_t*)(cache + 16 * (size_t)F.cap);
+    uint32_t* c_off = (uint32_t*)(cache + 20 * (size_t)F.cap);
+    if (F.staged) {
+        const uint32_t o0 = F.aoff[0];
+        for (int v = 0; v < n; ++v) {
+            const uint32_t ov = F.aoff[v], cv = F.acnt[v];
+            if (lane == 0) c_off[v] = ov - o0;
+            for (uint32_t j = lane; j < cv; j += 32) {
+                const uint32_t r = S.srank[(size_t)v * S.Sp + F.aspos[ov + j]];
+                c_mask[ov - o0 + j] = F.amask[ov + j];
+                c_rank[ov - o0 + j] = r;
+                c_key[ov - o0 + j] = S.keys[(size_t)v * S.Sp + r];
+            }
+        }
+        if (lane == 0) c_off[n] = F.aoff[n - 1] + F.acnt[n - 1] - o0;
+    }
+    for (int i = lane; i < n; i += 32) {
+        W.ord[i] = S.cur_order[(size_t)c * n + i];
+        W.rank[i] = S.cur_rank[(size_t)c * n + i];
+        W.key[i] = S.cur_key[(size_t)c * n + i];
+        W.since[i] = F.t0;
+    }
+    double score = S.cur_score[c], best = S.best_score[c];
+    int64_t acc_count = 0, items = 0;
+    __syncwarp();
+    for (int it = 0; it < F.iters; ++it) {
+        const int64_t t = F.t0 + it;
+        const U64x4 x = philox4x64((uint64_t)t, (uint64_t)c, 0, 0, S.seed, 0);
+        int a, b;
+        pair_decode(n, __umul64hi(x.x[0], P), a, b);
+        // proposed order on the lanes (positions lane, lane + 32) and prefix masks
+        int v[2];
+        uint64_t bit[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = lane + 32 * h;
+            v[h] = 0;
+            bit[h] = 0;
+            if (p < n) {
+                v[h] = W.ord[(p == a) ? b : (p == b) ? a : p];
+                bit[h] = 1ull << v[h];
+            }
+        }
+        uint64_t s0 = bit[0], s1 = bit[1];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t t0 = __shfl_up_sync(0xffffffffu, s0, off);
+            const uint64_t t1 = __shfl_up_sync(0xffffffffu, s1, off);
+            if (lane >= off) { s0 |= t0; s1 |= t1; }
+        }
+        const uint64_t first_half = __shfl_sync(0xffffffffu, s0, 31);
+        uint32_t nrank[2] = {0, 0};
+        // keys of the proposal: unaffected nodes keep theirs, the span a..b is re-scored
+        for (int i = lane; i < n; i += 32) W.nkey[i] = W.key[i];
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = lane + 32 * h;
+            if (p < n && p >= a && p <= b) {
+                const int node = v[h];
+                const uint64_t excl = (h == 0 ? s0 : (s1 | first_half)) & ~bit[h];
+                const uint64_t npc = ~compress_pred(excl, node);
+                if (F.staged) {
+                    // survivors of the node in score order: the first consistent one wins
+                    const uint32_t j1 = c_off[node + 1];
+                    uint32_t j = c_off[node];
+                    while (j + 1 < j1 && (c_mask[j] & npc) != 0ull) ++j;
+                    nrank[h] = c_rank[j];
+                    W.nkey[node] = c_key[j];
+                } else {
+                    const uint64_t* M = F.amask + F.aoff[node];
+                    const uint32_t cnt = F.acnt[node];
+                    uint32_t sp = 0;
+                    for (uint32_t j = 0; j < cnt; ++j) {
+                        if ((M[j] & npc) == 0ull) { sp = F.aspos[F.aoff[node] + j]; break; }
+                    }
+                    nrank[h] = S.srank[(size_t)node * S.Sp + sp];
+                    W.nkey[node] = S.keys[(size_t)node * S.Sp + nrank[h]];
+                }
+            }
+        }
+        __syncwarp();
+        int acc = 0;
+        double s2 = 0.0;
+        if (lane == 0) {
+            for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+            const double delta = __dsub_rn(s2, score);
+            const double lu = log(__dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52));
+            acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+        }
+        acc = __shfl_sync(0xffffffffu, acc, 0);
+        s2 = __shfl_sync(0xffffffffu, s2, 0);
+        items += b - a + 1;
+        if (acc) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int p = lane + 32 * h;
+                if (p < n && p >= a && p <= b) {
+                    const int node = v[h];
+                    if (nrank[h] != W.rank[node]) {
+                        credit_edges(S, c, node, W.rank[node], W.since[node], t);
+                        W.since[node] = t;
+                        W.rank[node] = nrank[h];
+                    }
+                    W.key[node] = W.nkey[node];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const uint8_t oa = W.ord[a];
+                W.ord[a] = W.ord[b];
+                W.ord[b] = oa;
+            }
+            __syncwarp();
+            score = s2;
+            ++acc_count;
+            if (s2 > best) {
+                best = s2;
+                for (int i = lane; i < n; i += 32) {
+                    S.best_order[(size_t)c * n + i] = W.ord[i];
+                    S.best_rank[(size_t)c * n + i] = W.rank[i];
+                }
+            }
+        }
+        if (lane == 0 && t < S.trace_cap) {
+            S.trace_score[(size_t)c * S.trace_cap + t] = score;
+            S.trace_accept[(size_t)c * S.trace_cap + t] = (uint8_t)acc;
+        }
+        if (t >= S.burn_in && S.record_every > 0 && ((t - S.burn_in) % S.record_every) == 0 &&
+            (t - S.burn_in) / S.record_every < S.record_cap) {
+            const int64_t ridx = (t - S.burn_in) / S.record_every;
+            for (int i = lane; i < n; i += 32) {
+                uint64_t m = S.pst[W.rank[i]];
+                while (m) {
+                    const int slot = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const int par = slot + (slot >= i ? 1 : 0);
+                    S.rec_bits[(((size_t)c * n + i) * n + par) * S.rec_words + (ridx >> 6)] |= 1ull << (ridx & 63);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    const int64_t t_end = F.t0 + F.iters;
+    for (int i = lane; i < n; i += 32) {
+        credit_edges(S, c, i, W.rank[i], W.since[i], t_end);
+        S.cur_order[(size_t)c * n + i] = W.ord[i];
+        S.cur_rank[(size_t)c * n + i] = W.rank[i];
+        S.cur_key[(size_t)c * n + i] = W.key[i];
+    }
+    if (lane == 0) {
+        S.cur_score[c] = score;
+        S.best_score[c] = best;
+        S.accepts[c] += acc_count;
+        atomicAdd((unsigned long long*)S.items_total, (unsigned long long)items);
+    }
+}
+
+__host__ __device__ constexpr size_t surv_cache_stride(int cap) { return (surv_cache_bytes(cap) + 15) / 16 * 16; }
+
+__global__ void __launch_bounds__(32 * FUSED_WARPS) k_chain_fused(ChainState S, FusedArgs F)
+{
+    __shared__ FusedSmem sm[FUSED_WARPS];
+    extern __shared__ __align__(16) uint8_t fcache[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * FUSED_WARPS + warp;
+    if (c >= S.C) return;
+    chain_fused_body(S, F, c, lane, sm[warp], fcache + warp * surv_cache_stride(F.cap));
+}
+
+// many networks' chains in one launch: global warp g belongs to the network i with
+// base[i] <= g < base[i + 1] (chain g - base[i] of that network)
+__global__ void __launch_bounds__(32 * FUSED_WARPS) k_batch_fused(const ChainState* __restrict__ Ss,
+                                                                 const FusedArgs* __restrict__ Fs,
+                                                                 const int64_t* __restrict__ base, int nnet)
+{
+    __shared__ FusedSmem sm[FUSED_WARPS];
+    extern __shared__ __align__(16) uint8_t fcache[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * FUSED_WARPS + warp;
+    if (g >= base[nnet]) return;
+    int lo = 0, hi = nnet;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    const ChainState S = Ss[lo];
+    const FusedArgs F = Fs[lo];
+    chain_fused_body(S, F, (int)(g - base[lo]), lane, sm[warp], fcache + warp * surv_cache_stride(F.cap));
+}
+
+// the survivor cache of a launch: every network of it uses one layout (the largest that
+// fits); networks with more survivors walk them in global memory
+static int fused_smem_setup(int cap, size_t* smem)
+{
+    static bool done[64] = {false};
+    const int d = device_id();
+    const size_t mx = FUSED_WARPS * surv_cache_stride(SURV_CAP_MAX);
+    if (d < 64 && !done[d]) {
+        BN_CUDA(cudaFuncSetAttribute(k_chain_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        done[d] = true;
+    }
+    *smem = FUSED_WARPS * surv_cache_stride(cap);
+    return BN_OK;
+}
+
+__global__ void k_batch_advance(const ChainState* __restrict__ Ss, const int* __restrict__ iters, int nnet)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnet || iters[i] == 0) return;
+    const ChainState& S = Ss[i];
+    const int64_t t_end = *S.step + iters[i];
+    *S.step = t_end;
+    if (S.record_every > 0 && t_end > S.burn_in) {
+        const int64_t r = (t_end - 1 - S.burn_in) / S.record_every + 1;
+        *S.rec_count = r < S.record_cap ? r : S.record_cap;
+    }
+}
+
+// after a fused launch: the step counter and the number of recorded states
+__global__ void k_step_advance(ChainState S, int64_t iters)
+{
+    const int64_t t_end = *S.step + iters;
+    *S.step = t_end;
+    if (S.record_every > 0 && t_end > S.burn_in) {
+        const int64_t r = (t_end - 1 - S.burn_in) / S.record_every + 1;
+        *S.rec_count = r < S.record_cap ? r : S.record_cap;
+    }
+}
+
 // learned proposal, step 1: draw the pair from the cached q(. | current order) by inverse
 // CDF (one warp per chain), then the same swap and work lists as k_propose
 __global__ void k_propose_learned(ChainState S)
@@ -389,8 +686,10 @@ __global__ void k_train_batch(ChainState S)
     uint8_t* o = S.train_orders + (size_t)c * n;
     for (int p = 0; p < n; ++p) o[p] = po[p == a ? b : p == b ? a : p];
     S.train_pairs[c] = (uint32_t)(a * (2 * n - a - 1) / 2 + (b - a - 1));
+    // the swap's acceptance probability, but 0 for swaps that change no parent set
+    // (always accepted, they move nothing)
     const float d = S.delta[c];
-    S.train_alpha[c] = d >= 0.f ? 1.f : exp10f(d);
+    S.train_alpha[c] = S.changed[c] ? (d >= 0.f ? 1.f : exp10f(d)) : 0.f;
 }
 
 // Geyer initial monotone sequence ESS of each recorded edge-indicator series, summed over
@@ -516,6 +815,38 @@ struct bn_chains {
     int64_t steps = 0;
     int dev = 0;
 };
+
+static constexpr int FUSED_ITERS = 256;     // MH steps per fused launch
+
+static bool fused_path(const bn_chains* ch)
+{
+    return ch->S.mode == BN_PROPOSAL_UNIFORM && ch->t->scan_mode == BN_SCAN_PRUNED;
+}
+
+// `iters` fused steps starting at step t0; ev0/ev1 (optional) bracket the fused kernel
+static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                        cudaEvent_t ev1 = nullptr)
+{
+    FusedArgs F;
+    F.amask = ch->t->amask;
+    F.aspos = ch->t->aspos;
+    F.aoff = ch->t->aoff;
+    F.acnt = ch->t->acnt;
+    F.t0 = t0;
+    F.iters = iters;
+    F.staged = ch->t->alive_total <= SURV_CAP_MAX ? 1 : 0;
+    F.cap = F.staged ? (int)ch->t->alive_total : 0;
+    size_t smem = 0;
+    int rc = fused_smem_setup(F.cap, &smem);
+    if (rc) return rc;
+    if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
+    k_chain_fused<<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
+    BN_LAUNCH_CHECK("k_chain_fused");
+    if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
+    k_step_advance<<<1, 1, 0, s>>>(ch->S, iters);
+    BN_LAUNCH_CHECK("k_step_advance");
+    return BN_OK;
+}
 
 // one MH step of every chain; ev0/ev1 (optional) bracket the scan launch
 static int sweep_launch(bn_chains* ch, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
@@ -686,6 +1017,17 @@ extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
             if (s) cudaStreamDestroy(s);
         }
     } own_guard{own};
+    if (fused_path(ch)) {
+        for (int64_t done = 0; done < steps;) {
+            const int it = (int)std::min<int64_t>(FUSED_ITERS, steps - done);
+            int rc = fused_launch(ch, ch->steps + done, it, s);
+            if (rc) return rc;
+            done += it;
+        }
+        ch->steps += steps;
+        BN_CUDA(cudaStreamSynchronize(s));
+        return BN_OK;
+    }
     if (ch->exec && ch->exec_scan_mode != ch->t->scan_mode) {
         cudaGraphExecDestroy(ch->exec);
         ch->exec = nullptr;
@@ -732,22 +1074,34 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
             for (auto e : v) cudaEventDestroy(e);
         }
     } ev_guard{ev};
-    for (int64_t i = 0; i < steps; ++i) {
-        int rc = sweep_launch(ch, s, ev[2 * i], ev[2 * i + 1]);
-        if (rc) return rc;
+    int64_t launches = steps;
+    if (fused_path(ch)) {
+        // the fused kernel is the whole step: its launches are what the events bracket
+        launches = 0;
+        for (int64_t done = 0; done < steps; ++launches) {
+            const int it = (int)std::min<int64_t>(FUSED_ITERS, steps - done);
+            int rc = fused_launch(ch, ch->steps + done, it, s, ev[2 * launches], ev[2 * launches + 1]);
+            if (rc) return rc;
+            done += it;
+        }
+    } else {
+        for (int64_t i = 0; i < steps; ++i) {
+            int rc = sweep_launch(ch, s, ev[2 * i], ev[2 * i + 1]);
+            if (rc) return rc;
+        }
     }
     ch->steps += steps;
     uint32_t st = 0;
     BN_CUDA(cudaMemcpyAsync(&st, ch->S.status, 4, cudaMemcpyDeviceToHost, s));
     BN_CUDA(cudaStreamSynchronize(s));
     double tot = 0.0;
-    for (int64_t i = 0; i < steps; ++i) {
+    for (int64_t i = 0; i < launches; ++i) {
         float ms = 0.f;
         BN_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
         tot += ms;
     }
     if (scan_ms) *scan_ms = tot;
-    if (scan_launches) *scan_launches = steps;
+    if (scan_launches) *scan_launches = launches;
     if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_chains_step_profiled: a bounded device wait expired");
     return BN_OK;
 }
@@ -841,7 +1195,8 @@ extern "C" int bn_chains_set_proposal(bn_chains* ch, bn_mlp* m, int mode, double
             return o;
         };
         const size_t o_cur = take(4 * C * P), o_prop = take(4 * C * P), o_pair = take(4 * C), o_lqf = take(4 * C),
-                     o_delta = take(4 * C), o_to = take(C * S.n), o_tp = take(4 * C), o_ta = take(4 * C);
+                     o_delta = take(4 * C), o_to = take(C * S.n), o_tp = take(4 * C), o_ta = take(4 * C),
+                     o_ch = take(C);
         cudaError_t e = cudaMalloc(&ch->prop_block, off);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -857,6 +1212,7 @@ extern "C" int bn_chains_set_proposal(bn_chains* ch, bn_mlp* m, int mode, double
         S.train_orders = B + o_to;
         S.train_pairs = (uint32_t*)(B + o_tp);
         S.train_alpha = (float*)(B + o_ta);
+        S.changed = B + o_ch;
         BN_CUDA(cudaMemsetAsync(ch->prop_block, 0, off, s));
     }
     ch->mlp = m;
@@ -912,4 +1268,122 @@ extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t s
     cudaFreeAsync(d_f, s);
     BN_CUDA(cudaStreamSynchronize(s));
     return BN_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// batches of networks of uneven size
+// ---------------------------------------------------------------------------------
+struct bn_batch {
+    std::vector<bn_chains*> chains;
+    void* dev = nullptr;            // device arrays: ChainState[], FusedArgs[], base[], iters[]
+    size_t dev_bytes = 0;
+};
+
+extern "C" int bn_batch_create(int count, const bn_table* const* tables, const bn_mcmc_params* params, void* stream,
+                               bn_batch** out)
+{
+    set_error(BN_OK, "");
+    if (!out || count < 1 || !tables || !params) return set_error(BN_EINVAL, "bn_batch_create: bad arguments");
+    *out = nullptr;
+    bn_batch* b = new bn_batch();
+    for (int i = 0; i < count; ++i) {
+        bn_chains* c = nullptr;
+        int rc = bn_chains_create(tables[i], &params[i], nullptr, BN_MEM_HOST, stream, &c);
+        if (rc) {
+            bn_batch_free(b);
+            return rc;
+        }
+        b->chains.push_back(c);
+    }
+    const size_t bytes = (sizeof(ChainState) + sizeof(FusedArgs) + 2 * sizeof(int64_t)) * (size_t)(count + 1) + 1024;
+    cudaError_t e = cudaMalloc(&b->dev, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bn_batch_free(b);
+        return set_error(BN_ENOMEM, "bn_batch_create: %zu bytes", bytes);
+    }
+    b->dev_bytes = bytes;
+    *out = b;
+    return BN_OK;
+}
+
+extern "C" int bn_batch_chains(bn_batch* b, int i, bn_chains** out)
+{
+    if (!b || !out || i < 0 || i >= (int)b->chains.size()) return set_error(BN_EINVAL, "bn_batch_chains: bad index");
+    *out = b->chains[i];
+    return BN_OK;
+}
+
+extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
+{
+    set_error(BN_OK, "");
+    if (!b || steps < 0) return set_error(BN_EINVAL, "bn_batch_step: bad arguments");
+    if (steps == 0) return BN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<bn_chains*> fused, other;
+    for (bn_chains* c : b->chains) (fused_path(c) ? fused : other).push_back(c);
+    // networks on other proposals step through their own per-network path
+    for (bn_chains* c : other) {
+        int rc = bn_chains_step(c, steps, stream);
+        if (rc) return rc;
+    }
+    if (fused.empty()) return BN_OK;
+    const int nf = (int)fused.size();
+    std::vector<ChainState> hs(nf);
+    std::vector<int64_t> base(nf + 1, 0);
+    for (int i = 0; i < nf; ++i) {
+        hs[i] = fused[i]->S;
+        base[i + 1] = base[i] + fused[i]->S.C;
+    }
+    uint8_t* d = (uint8_t*)b->dev;
+    ChainState* d_states = (ChainState*)d;
+    FusedArgs* d_fargs = (FusedArgs*)(d + sizeof(ChainState) * (nf + 1));
+    int64_t* d_base = (int64_t*)((uint8_t*)d_fargs + sizeof(FusedArgs) * (nf + 1));
+    int* d_iters = (int*)(d_base + nf + 1);
+    BN_CUDA(cudaMemcpyAsync(d_states, hs.data(), sizeof(ChainState) * nf, cudaMemcpyHostToDevice, s));
+    BN_CUDA(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, s));
+    std::vector<FusedArgs> hf(nf);
+    std::vector<int> hit(nf);
+    const unsigned blocks = (unsigned)((base[nf] + FUSED_WARPS - 1) / FUSED_WARPS);
+    int cap = 0;
+    for (bn_chains* c : fused)
+        if (c->t->alive_total <= SURV_CAP_MAX) cap = std::max(cap, (int)c->t->alive_total);
+    size_t smem = 0;
+    {
+        int rc = fused_smem_setup(cap, &smem);
+        if (rc) return rc;
+    }
+    for (int64_t done = 0; done < steps;) {
+        const int it = (int)std::min<int64_t>(FUSED_ITERS, steps - done);
+        for (int i = 0; i < nf; ++i) {
+            const bn_table* t = fused[i]->t;
+            hf[i].amask = t->amask;
+            hf[i].aspos = t->aspos;
+            hf[i].aoff = t->aoff;
+            hf[i].acnt = t->acnt;
+            hf[i].t0 = fused[i]->steps + done;
+            hf[i].iters = it;
+            hf[i].staged = t->alive_total <= cap ? 1 : 0;
+            hf[i].cap = cap;
+            hit[i] = it;
+        }
+        BN_CUDA(cudaMemcpyAsync(d_fargs, hf.data(), sizeof(FusedArgs) * nf, cudaMemcpyHostToDevice, s));
+        BN_CUDA(cudaMemcpyAsync(d_iters, hit.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s));
+        k_batch_fused<<<blocks, 32 * FUSED_WARPS, smem, s>>>(d_states, d_fargs, d_base, nf);
+        BN_LAUNCH_CHECK("k_batch_fused");
+        k_batch_advance<<<(nf + 127) / 128, 128, 0, s>>>(d_states, d_iters, nf);
+        BN_LAUNCH_CHECK("k_batch_advance");
+        BN_CUDA(cudaStreamSynchronize(s));     // the host argument arrays are reused
+        done += it;
+    }
+    for (bn_chains* c : fused) c->steps += steps;
+    return BN_OK;
+}
+
+extern "C" void bn_batch_free(bn_batch* b)
+{
+    if (!b) return;
+    for (bn_chains* c : b->chains) bn_chains_free(c);
+    cudaFree(b->dev);
+    delete b;
 }

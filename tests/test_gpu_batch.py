@@ -1,0 +1,80 @@
+"""Batches of networks of uneven size, n, arity, m and k: every network's chains in one
+fused launch must produce exactly what stepping each network alone produces, and a
+network switched to the learned proposal steps through its own path inside the batch."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+OUTS = ("trace_score", "trace_accept", "orders", "scores", "best_scores", "best_orders", "best_ranks", "accepts",
+        "edge_counts", "steps", "items")
+
+
+def _nets(count, seed, nmax=24):
+    out = []
+    rng = np.random.default_rng(seed)
+    for t in range(count):
+        n = int(rng.integers(6, nmax + 1))
+        ar = rng.integers(2, 5, size=n).astype(np.uint8)
+        m = int(rng.integers(50, 400))
+        k = int(rng.integers(2, 5))
+        net = synth.random_network(n, 3, ar, seed * 100 + t)
+        out.append((synth.forward_sample(net, m, seed * 100 + t + 1), ar, k))
+    return out
+
+
+def test_batch_equals_networks_alone(gpu):
+    nets = _nets(7, 3)
+    tables = []
+    for data, ar, k in nets:
+        t = gpu.build_scores(data, ar, k)
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+        tables.append(t)
+    chains = [5, 32, 1, 17, 64, 3, 40]
+    seeds = [11 * i + 1 for i in range(len(tables))]
+    b = gpu.batch_create(tables, chains, seeds, burn_in=20, trace_cap=400)
+    for s in (150, 250):
+        b.step(s)
+    for i, t in enumerate(tables):
+        alone = gpu.chains_create(t, chains[i], seeds[i], burn_in=20, trace_cap=400)
+        gpu.chains_step(alone, 400)
+        for what in OUTS:
+            assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
+
+
+def test_batch_network_vs_oracle(gpu):
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    tab = oracle.build_table(data, arity, k, R=R)
+    t6 = synth.workload("n6_k2_m100")
+    tab6 = oracle.build_table(t6[0], t6[1], t6[2])
+    ta = gpu.table_from_scores(tab, k)
+    tb = gpu.table_from_scores(tab6, t6[2])
+    for t in (ta, tb):
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    b = gpu.batch_create([ta, tb], [6, 4], [77, 78], burn_in=10, trace_cap=300)
+    b.step(300)
+    ref = oracle.mcmc_run(tab, k, 6, 300, seed=77, burn_in=10, trace=True)
+    assert np.array_equal(gpu.chains_read(b.chains(0), "trace_score"), ref["trace_score"])
+    assert np.array_equal(gpu.chains_read(b.chains(0), "edge_counts").astype(np.uint64), ref["edge_counts"])
+    ref6 = oracle.mcmc_run(tab6, t6[2], 4, 300, seed=78, burn_in=10, trace=True)
+    assert np.array_equal(gpu.chains_read(b.chains(1), "trace_score"), ref6["trace_score"])
+
+
+def test_batch_with_a_learned_network(gpu):
+    nets = _nets(3, 5)
+    tables = []
+    for data, ar, k in nets:
+        t = gpu.build_scores(data, ar, k)
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+        tables.append(t)
+    b = gpu.batch_create(tables, 16, 9)
+    n1 = gpu.table_info(tables[1])["n"]
+    net = gpu.mlp_create(n1, synth.mlp_init_weights(n1, 8, 128, 2), hidden=128, d=8, batch_cap=16)
+    gpu.chains_set_proposal(b.chains(1), net, gpu.PROPOSAL_LEARNED, eps_mix=0.2)
+    b.step(200)
+    for i in range(3):
+        assert gpu.chains_read(b.chains(i), "steps")[0] == 200
+        assert gpu.chains_read(b.chains(i), "accepts").max() > 0

@@ -90,6 +90,25 @@ def test_pruned_sampler_trajectories_vs_oracle(gpu):
     assert np.array_equal(gpu.chains_read(ch, "edge_counts").astype(np.uint64), ref["edge_counts"])
 
 
+def test_fused_steps_equal_batched_steps(gpu):
+    """Uniform proposals on a pruned table run as fused multi-step launches (one warp
+    per chain); every output must equal the per-step batched path on the full table."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    kw = dict(burn_in=30, record_every=3, record_cap=200, trace_cap=600)
+    a = gpu.chains_create(t, 64, 4242, **kw)
+    gpu.chains_step(a, 600)                                  # batched, full scan
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    b = gpu.chains_create(t, 64, 4242, **kw)
+    for s in (100, 7, 300, 193):                             # fused, across chunk boundaries
+        gpu.chains_step(b, s)
+    for what in ("trace_score", "trace_accept", "orders", "scores", "ranks", "best_orders", "best_scores",
+                 "best_ranks", "accepts", "edge_counts", "record", "record_len", "steps", "items"):
+        assert np.array_equal(gpu.chains_read(a, what), gpu.chains_read(b, what)), what
+    ea, eb = gpu.chains_read(a, "ess"), gpu.chains_read(b, "ess")
+    assert np.array_equal(np.isnan(ea), np.isnan(eb)) and np.allclose(ea[~np.isnan(ea)], eb[~np.isnan(eb)])
+
+
 def test_switching_mode_recaptures_the_step(gpu):
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     t = gpu.build_scores(data, arity, k, R=R)
