@@ -112,14 +112,19 @@ __device__ __forceinline__ U64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c
     return o;
 }
 
-// pair index p in [0, n(n-1)/2) -> positions a < b, lexicographic pair order
+// pair index p in [0, n(n-1)/2) -> positions a < b, lexicographic pair order.  Row a
+// starts at st(a) = a (2n - a - 1) / 2; a = max{a : st(a) <= p} from the quadratic's
+// root in FP32, then made exact with integer comparisons.
 __device__ __forceinline__ void pair_decode(int n, uint64_t p, int& a, int& b)
 {
-    int x = 0;
-    uint64_t row = (uint64_t)(n - 1);
-    while (p >= row) { p -= row; ++x; --row; }
+    const int ip = (int)p;
+    const float m = (float)(2 * n - 1);
+    int x = (int)floorf(0.5f * (m - sqrtf(fmaxf(m * m - 8.0f * (float)ip, 0.0f))));
+    x = max(0, min(x, n - 2));
+    while (x > 0 && x * (2 * n - x - 1) / 2 > ip) --x;
+    while (x + 1 <= n - 2 && (x + 1) * (2 * n - x - 2) / 2 <= ip) ++x;
     a = x;
-    b = x + 1 + (int)p;
+    b = x + 1 + (ip - x * (2 * n - x - 1) / 2);
 }
 
 // ---------------------------------------------------------------------------------

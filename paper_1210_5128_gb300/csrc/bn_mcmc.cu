@@ -333,7 +333,16 @@ struct FusedArgs {
     int iters;
     int staged;          // 1: the network's survivors fit the warp's shared-memory cache
     int cap;             // survivors per warp cache (shared-memory layout of the launch)
+    double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
 };
+
+// rounding bound of the MH test's right-hand side: two sequential sums of n entries of
+// magnitude <= max_abs (each within (n - 1) 2^-53 n max_abs) and the change summed over
+// the re-scored nodes, times ln 10, with a factor 8 to spare
+static double mh_margin(int n, double max_abs)
+{
+    return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52;
+}
 
 // per-warp shared-memory cache of a network's survivors: candidate mask, rank and key of
 // every survivor, and the node offsets
@@ -456,13 +465,41 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             }
         }
         __syncwarp();
+        // MH test.  The exact test compares ln u with ln10 (s' - s), s' the FP64 sum over
+        // nodes in ascending id.  Most steps are decided without it: the change of the
+        // re-scored nodes alone (any summation order) is within ~n eps sum|entries| of
+        // s' - s and an FP32 log(u) within 1e-6 (1 + |ln u|) of ln u; when the two sides
+        // are farther apart than both errors the decision is the exact one.  Close calls
+        // and accepted moves (whose new score the state keeps) take the exact path.
+        double dpart = 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = lane + 32 * h;
+            if (p < n && p >= a && p <= b)
+                dpart += key_to_double(W.nkey[v[h]]) - key_to_double(W.key[v[h]]);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
         int acc = 0;
         double s2 = 0.0;
         if (lane == 0) {
-            for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
-            const double delta = __dsub_rn(s2, score);
-            const double lu = log(__dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52));
-            acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+            const double u = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
+            const float luf = logf((float)u);
+            const double xa = S.literal_log ? dpart : LN10 * dpart;
+            const double margin = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
+            const double gap = (double)luf - xa;
+            int exact = 0;
+            if (gap > margin) acc = 0;
+            else if (gap < -margin) { acc = 1; exact = 1; }
+            else exact = 2;
+            if (exact) {
+                for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+                if (exact == 2) {
+                    const double delta = __dsub_rn(s2, score);
+                    const double lu = log(u);
+                    acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+                }
+            }
         }
         acc = __shfl_sync(0xffffffffu, acc, 0);
         s2 = __shfl_sync(0xffffffffu, s2, 0);
@@ -836,6 +873,7 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     F.iters = iters;
     F.staged = ch->t->alive_total <= SURV_CAP_MAX ? 1 : 0;
     F.cap = F.staged ? (int)ch->t->alive_total : 0;
+    F.margin_x = mh_margin(ch->S.n, ch->t->max_abs_survivor);
     size_t smem = 0;
     int rc = fused_smem_setup(F.cap, &smem);
     if (rc) return rc;
@@ -1365,6 +1403,7 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
             hf[i].iters = it;
             hf[i].staged = t->alive_total <= cap ? 1 : 0;
             hf[i].cap = cap;
+            hf[i].margin_x = mh_margin(t->n, t->max_abs_survivor);
             hit[i] = it;
         }
         BN_CUDA(cudaMemcpyAsync(d_fargs, hf.data(), sizeof(FusedArgs) * nf, cudaMemcpyHostToDevice, s));

@@ -31,8 +31,9 @@ static constexpr uint32_t TC_IDESC = tc_idesc_bf16_f32(TC_BM, TC_BN);
 struct GemmArgs {
     const bf16* A;   // M x K, row stride lda (elements)
     const bf16* B;   // N x K, row stride ldb
-    float* C;        // M x N, row stride ldc
+    float* C;        // M x N, row stride ldc; with split-K: partials [split][M][N]
     int M, N, K, lda, ldb, ldc;
+    int ksplit;      // K / ksplit per CTA along grid z (1 = no split)
     uint32_t* status;
 };
 
@@ -49,7 +50,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g)
     uint32_t* tslot = (uint32_t*)(bar + TC_STAGES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
-    const int nk = g.K / TC_BK;
+    const int kpart = g.K / g.ksplit;               // this CTA's K range (multiple of 64)
+    const int kbase = blockIdx.z * kpart;
+    const int nk = kpart / TC_BK;
+    float* Cz = g.C + (size_t)blockIdx.z * g.M * g.ldc;
 
     if (warp == 0) {
         tc_alloc(tslot, 128);
@@ -69,8 +73,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g)
         uint8_t* b = sB + s * TC_TILE;
         for (int c = tid; c < TC_BM * 8; c += 128) {
             const int r = c >> 3, kc = c & 7;
-            cp_async16(a + tc_tile_off(r, kc), g.A + (size_t)(m0 + r) * g.lda + kt * TC_BK + kc * 8);
-            cp_async16(b + tc_tile_off(r, kc), g.B + (size_t)(n0 + r) * g.ldb + kt * TC_BK + kc * 8);
+            cp_async16(a + tc_tile_off(r, kc), g.A + (size_t)(m0 + r) * g.lda + kbase + kt * TC_BK + kc * 8);
+            cp_async16(b + tc_tile_off(r, kc), g.B + (size_t)(n0 + r) * g.ldb + kbase + kt * TC_BK + kc * 8);
         }
         cp_async_commit();
     };
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g)
             uint32_t r[32];
             tc_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             tc_wait_ld();
-            float* dst = g.C + (size_t)row * g.ldc + n0 + c0;
+            float* dst = Cz + (size_t)row * g.ldc + n0 + c0;
             if (nk > 0) {
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)
@@ -133,8 +137,22 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g)
     if (warp == 0) tc_dealloc(tmem, 128);
 }
 
+// C = sum over the split partials, in split order (deterministic)
+__global__ void k_splitk_reduce(const float* __restrict__ ws, int ksplit, int M, int N, float* __restrict__ C,
+                                int ldc)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * N) return;
+    const int r = (int)(idx / N), c = (int)(idx - (int64_t)r * N);
+    float s = 0.f;
+    for (int z = 0; z < ksplit; ++z) s += ws[(size_t)z * M * N + idx];
+    C[(size_t)r * ldc + c] = s;
+}
+
+// C = A B^T.  Few output tiles and a long K split K over grid z (each CTA at least four
+// 64-wide stages) into the workspace, then one reduction; ws == nullptr disables it.
 int gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, int M, int N, int K,
-            uint32_t* status, cudaStream_t s)
+            uint32_t* status, cudaStream_t s, float* ws, size_t ws_elems)
 {
     if (M % TC_BM || N % TC_BN || K % TC_BK)
         return set_error(BN_EINVAL, "gemm: M=%d N=%d K=%d must be multiples of 128, 128, 64", M, N, K);
@@ -144,9 +162,25 @@ int gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, i
         BN_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr[d] = true;
     }
-    GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc, status};
-    k_gemm_tc<<<dim3(N / TC_BN, M / TC_BM), 128, TC_SMEM, s>>>(g);
+    const int tiles = (M / TC_BM) * (N / TC_BN);
+    int split = 1;
+    if (ws) {
+        const int stages = K / TC_BK;
+        const int lim = std::min(sm_count() / std::max(tiles, 1), stages / 4);
+        for (int dv = lim; dv >= 2; --dv)
+            if (stages % dv == 0 && (size_t)dv * M * N <= ws_elems) {
+                split = dv;
+                break;
+            }
+    }
+    GemmArgs g{A, B, split > 1 ? ws : C, M, N, K, lda, ldb, split > 1 ? N : ldc, split, status};
+    k_gemm_tc<<<dim3(N / TC_BN, M / TC_BM, split), 128, TC_SMEM, s>>>(g);
     BN_LAUNCH_CHECK("k_gemm_tc");
+    if (split > 1) {
+        const int64_t tot = (int64_t)M * N;
+        k_splitk_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ws, split, M, N, C, ldc);
+        BN_LAUNCH_CHECK("k_splitk_reduce");
+    }
     return BN_OK;
 }
 
@@ -319,14 +353,14 @@ int bn::mlp_forward_dev(bn_mlp* m, const uint8_t* d_orders, int B, bool keep_tra
                                                       keep_transposes ? m->XT : nullptr);
     BN_LAUNCH_CHECK("k_embed");
     int rc;
-    if ((rc = gemm_tc(m->X, m->ndp, m->W1b, m->ndp, m->Z1, m->H, Mp, m->H, m->ndp, m->status, s))) return rc;
+    if ((rc = gemm_tc(m->X, m->ndp, m->W1b, m->ndp, m->Z1, m->H, Mp, m->H, m->ndp, m->status, s, m->ws, m->ws_elems))) return rc;
     k_bias_relu<<<nblk((int64_t)Mp * m->H), 256, 0, s>>>(m->Z1, m->b1, Mp, m->H, B, m->H1,
                                                         keep_transposes ? m->H1T : nullptr);
     BN_LAUNCH_CHECK("k_bias_relu");
-    if ((rc = gemm_tc(m->H1, m->H, m->W2b, m->H, m->Z2, m->H, Mp, m->H, m->H, m->status, s))) return rc;
+    if ((rc = gemm_tc(m->H1, m->H, m->W2b, m->H, m->Z2, m->H, Mp, m->H, m->H, m->status, s, m->ws, m->ws_elems))) return rc;
     k_bias_relu<<<nblk((int64_t)Mp * m->H), 256, 0, s>>>(m->Z2, m->b2, Mp, m->H, B, m->H2, nullptr);
     BN_LAUNCH_CHECK("k_bias_relu");
-    if ((rc = gemm_tc(m->H2, m->H, m->W3b, m->H, m->L, m->Pp, Mp, m->Pp, m->H, m->status, s))) return rc;
+    if ((rc = gemm_tc(m->H2, m->H, m->W3b, m->H, m->L, m->Pp, Mp, m->Pp, m->H, m->status, s, m->ws, m->ws_elems))) return rc;
     k_bias<<<nblk((int64_t)Mp * m->Pp), 256, 0, s>>>(m->L, m->b3, Mp, m->Pp);
     BN_LAUNCH_CHECK("k_bias");
     return BN_OK;
@@ -348,15 +382,15 @@ int bn::mlp_loss_grad_dev(bn_mlp* m, const uint8_t* d_orders, const uint32_t* d_
     k_colsum<<<nblk(H), 256, 0, s>>>(m->dZ2, H, B, m->gb2);
     BN_LAUNCH_CHECK("k_colsum");
     // dW2 = dZ2^T H1 ; dH1 = dZ2 W2
-    if ((rc = gemm_tc(m->dZ2T, Mp, m->H1T, Mp, m->gW2, H, H, H, Mp, m->status, s))) return rc;
-    if ((rc = gemm_tc(m->dZ2, H, m->W2T, H, m->dH1, H, Mp, H, H, m->status, s))) return rc;
+    if ((rc = gemm_tc(m->dZ2T, Mp, m->H1T, Mp, m->gW2, H, H, H, Mp, m->status, s, m->ws, m->ws_elems))) return rc;
+    if ((rc = gemm_tc(m->dZ2, H, m->W2T, H, m->dH1, H, Mp, H, H, m->status, s, m->ws, m->ws_elems))) return rc;
     k_relu_grad<<<nblk((int64_t)Mp * H), 256, 0, s>>>(m->dH1, m->Z1, Mp, H, B, m->dZ1, m->dZ1T);
     BN_LAUNCH_CHECK("k_relu_grad");
     k_colsum<<<nblk(H), 256, 0, s>>>(m->dZ1, H, B, m->gb1);
     BN_LAUNCH_CHECK("k_colsum");
     // dW1 = dZ1^T X ; dX = dZ1 W1
-    if ((rc = gemm_tc(m->dZ1T, Mp, m->XT, Mp, m->gW1, m->ndp, H, m->ndp, Mp, m->status, s))) return rc;
-    if ((rc = gemm_tc(m->dZ1, H, m->W1T, H, m->dX, m->ndp, Mp, m->ndp, H, m->status, s))) return rc;
+    if ((rc = gemm_tc(m->dZ1T, Mp, m->XT, Mp, m->gW1, m->ndp, H, m->ndp, Mp, m->status, s, m->ws, m->ws_elems))) return rc;
+    if ((rc = gemm_tc(m->dZ1, H, m->W1T, H, m->dX, m->ndp, Mp, m->ndp, H, m->status, s, m->ws, m->ws_elems))) return rc;
     k_embed_grad<<<nblk((int64_t)B * m->n * m->d), 256, 0, s>>>(d_orders, m->dX, B, m->n, m->d, m->ndp, m->gE);
     BN_LAUNCH_CHECK("k_embed_grad");
     return BN_OK;
@@ -420,7 +454,8 @@ extern "C" int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, cons
         {&m->mb1, (size_t)H}, {&m->mW2, nW2}, {&m->mb2, (size_t)H}, {&m->mW3, nW3}, {&m->mb3, (size_t)Pp},
         {&m->vE, nE}, {&m->vW1, nW1}, {&m->vb1, (size_t)H}, {&m->vW2, nW2}, {&m->vb2, (size_t)H},
         {&m->vW3, nW3}, {&m->vb3, (size_t)Pp}, {&m->Z1, (size_t)cap * H}, {&m->Z2, (size_t)cap * H},
-        {&m->L, (size_t)cap * Pp}, {&m->dH1, (size_t)cap * H}, {&m->dX, (size_t)cap * ndp}, {&m->loss, 4}};
+        {&m->L, (size_t)cap * Pp}, {&m->dH1, (size_t)cap * H}, {&m->dX, (size_t)cap * ndp}, {&m->loss, 4},
+        {&m->ws, (size_t)8 * cap * std::max(std::max(Pp, ndp), H)}};
     std::vector<std::pair<bf16**, size_t>> b16 = {
         {&m->Eb, nE}, {&m->W1b, nW1}, {&m->W1T, nW1}, {&m->W2b, nW2}, {&m->W2T, nW2}, {&m->W3b, nW3},
         {&m->X, (size_t)cap * ndp}, {&m->XT, (size_t)cap * ndp}, {&m->H1, (size_t)cap * H},
@@ -448,6 +483,7 @@ extern "C" int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, cons
     m->stage_pairs = (uint32_t*)(base + o_stage + (size_t)round_up((int64_t)cap * n, 256));
     m->stage_alpha = (float*)((uint8_t*)m->stage_pairs + (size_t)round_up((int64_t)cap * 4, 256));
     m->bytes = off;
+    m->ws_elems = (size_t)8 * cap * std::max(std::max(Pp, ndp), H);
     auto fail = [&](int rc) { bn_mlp_free(m); return rc; };
     if (cudaMemsetAsync(m->block, 0, off, s) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__));
     const cudaMemcpyKind kind = mem == BN_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -569,7 +605,7 @@ extern "C" int bn_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int 
     uint32_t* st = nullptr;
     BN_CUDA(cudaMallocAsync((void**)&st, 4, s));
     BN_CUDA(cudaMemsetAsync(st, 0, 4, s));
-    int rc = gemm_tc((const bf16*)A, K, (const bf16*)B, K, C, N, M, N, K, st, s);
+    int rc = gemm_tc((const bf16*)A, K, (const bf16*)B, K, C, N, M, N, K, st, s, nullptr, 0);
     uint32_t h = 0;
     if (!rc) {
         BN_CUDA(cudaMemcpyAsync(&h, st, 4, cudaMemcpyDeviceToHost, s));

@@ -21,6 +21,8 @@ struct bn_mlp {
     __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *dZ2, *dZ2T, *dZ1, *dZ1T;
     // FP32 activations
     float *Z1, *Z2, *L, *dH1, *dX, *loss;
+    float* ws = nullptr;           // split-K partials
+    size_t ws_elems = 0;
     uint32_t* status;
     uint8_t* stage_orders;
     uint32_t* stage_pairs;
@@ -29,7 +31,7 @@ struct bn_mlp {
 
 namespace bn {
 int gemm_tc(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M, int N,
-            int K, uint32_t* status, cudaStream_t s);
+            int K, uint32_t* status, cudaStream_t s, float* ws, size_t ws_elems);
 // forward of B orders (device pointer); logits land in m->L (row stride Pp)
 int mlp_forward_dev(bn_mlp* m, const uint8_t* d_orders, int B, bool keep_transposes, cudaStream_t s);
 int mlp_loss_grad_dev(bn_mlp* m, const uint8_t* d_orders, const uint32_t* d_pairs, const float* d_alpha, int B,

@@ -12,6 +12,7 @@
 // class by size class from the j immediate subsets; pi survives iff key(pi) >
 // max_t best_le(pi minus its t-th element).
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "bn_table.cuh"
@@ -143,6 +144,20 @@ __global__ void __launch_bounds__(256) k_alive_write(const uint8_t* __restrict__
             running += tot;
         }
         __syncthreads();
+    }
+}
+
+// largest |entry| among the survivors (positive doubles order like their bit patterns)
+__global__ void k_survivor_maxabs(const uint32_t* __restrict__ aspos, const uint32_t* __restrict__ aoff,
+                                  const uint32_t* __restrict__ acnt, const uint32_t* __restrict__ srank,
+                                  const int64_t* __restrict__ keys, int64_t Sp, int n, unsigned long long* out)
+{
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    for (uint32_t j = threadIdx.x; j < acnt[i]; j += blockDim.x) {
+        const uint32_t r = srank[(size_t)i * Sp + aspos[aoff[i] + j]];
+        const double v = fabs(key_to_double(keys[(size_t)i * Sp + r]));
+        atomicMax(out, (unsigned long long)__double_as_longlong(v));
     }
 }
 
@@ -289,7 +304,16 @@ int prune_table(bn_table* t, cudaStream_t s)
     BN_CUDA(cudaMemcpyAsync(d_offs, ho.data(), 4 * ho.size(), cudaMemcpyHostToDevice, s));
     k_alive_write<<<n * nch, 256, 0, s>>>(alive, t->srank, t->pst, S, Sp, nch, d_offs, t->amask, t->aspos);
     BN_LAUNCH_CHECK("k_alive_write");
+    unsigned long long* d_mx = (unsigned long long*)binom;          // reuse: one word
+    BN_CUDA(cudaMemsetAsync(d_mx, 0, 8, s));
+    k_survivor_maxabs<<<n, 128, 0, s>>>(t->aspos, t->aoff, t->acnt, t->srank, t->keys, Sp, n, d_mx);
+    BN_LAUNCH_CHECK("k_survivor_maxabs");
+    unsigned long long hmx = 0;
+    BN_CUDA(cudaMemcpyAsync(&hmx, d_mx, 8, cudaMemcpyDeviceToHost, s));
     BN_CUDA(cudaStreamSynchronize(s));
+    double mx_abs;
+    memcpy(&mx_abs, &hmx, 8);
+    t->max_abs_survivor = mx_abs;
     (void)offs;
     return BN_OK;
 }

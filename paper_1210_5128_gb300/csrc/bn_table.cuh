@@ -25,6 +25,7 @@ struct bn_table {
     uint32_t alive_max = 0;
     int alive_chunks = 1;
     void* alive_block = nullptr;
+    double max_abs_survivor = 0.0;   // largest |entry| among the survivors
     // full-scan tiling chosen by bn_table_autotune, per number of 256-item groups (1..8);
     // tuned_sub == 0: not tuned
     int tuned_sub[9] = {0};
