@@ -182,22 +182,37 @@ def config_dict(chains, scan="pruned"):
                         f"k=4 (489,406 parent sets/node, 29.36M FP64 entries, 235 MB), {chains} chains, "
                         "uniform swap proposal",
             "chains": chains, "n": 60, "k": 4, "m": 1000, "scan": scan,
-            "l2": "inputs larger than L2 (235 MB table; full-scan steps stream it every step)"}
+            "l2": "flushed: a 512 MB buffer is written before every timed step (outside its events); "
+                  "the table is 235 MB of FP64 entries, the full scan streams 117 MB of sorted positions "
+                  "plus the 3.9 MB mask table per pass"}
 
 
 ALU_LANES_PER_SM = 64      # 32-bit logic / compare / min-max results per clock per SM
 SCAN_ALU_OPS = 3           # per (entry, item) test: 64-bit AND-NOT + zero test (2), min (1)
+L2_FLUSH_BYTES = 512 << 20 # written between timed steps (L2 is 129 MB)
 
 
-def _timed(bn, torch, chains, steps, stream):
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    bn.chains_step(chains, steps, stream=stream.cuda_stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+def _timed(bn, torch, chains, steps, stream, pieces=1, flush=None):
+    """Device time (ms) of `steps` MH steps run as `pieces` calls, each bracketed by CUDA
+    events on the launching stream; with `flush`, L2 is overwritten before every piece,
+    outside the events."""
+    total = 0.0
+    done = 0
+    for p in range(pieces):
+        k = (steps - done) // (pieces - p)
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.add_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bn.chains_step(chains, k, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        done += k
+    return total
 
 
 def _ess_run(bn, torch, table, chains, seed, pre_steps, steps, stream, net=None, train_steps=0, thin=1):
@@ -280,7 +295,8 @@ def main():
         full = bn.chains_create(table, args.chains, seed=seed)
         bn.chains_step(full, args.warmup, stream=stream.cuda_stream)
         i0 = int(bn.chains_read(full, "items")[0])
-        ms_full = _timed(bn, torch, full, args.steps, stream)
+        flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        ms_full = _timed(bn, torch, full, args.steps, stream, pieces=args.steps, flush=flush)
         items_full = int(bn.chains_read(full, "items")[0]) - i0
         prof_steps = max(20, min(args.steps, 100))
         i1 = int(bn.chains_read(full, "items")[0])
@@ -302,7 +318,7 @@ def main():
         clk = ClockSampler(local)
         clk.start()
         l0 = bn.kernel_launches()
-        ms = _timed(bn, torch, chains, args.steps * ips, stream)
+        ms = _timed(bn, torch, chains, args.steps * ips, stream, pieces=args.steps, flush=flush)
         launches = bn.kernel_launches() - l0
         barrier()
         clocks = clk.stop()

@@ -110,6 +110,13 @@ void bn_table_free(bn_table* t);
 int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
                     double* order_score, int mem, void* stream);
 
+/* bn_score_orders with the device time of its scan (the consistent-max kernel of Eq. (6),
+ * the call's dominant launch) measured by CUDA events on `stream` around that launch:
+ * *scan_ms receives it (0 for B = 0; scan_ms may be NULL).  Outputs and errors as
+ * bn_score_orders. */
+int bn_score_orders_profiled(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
+                             double* order_score, int mem, void* stream, double* scan_ms);
+
 /* bn_score_orders without any allocation.  The paper has no counterpart to this call.
  * It is for callers that cannot allocate device memory when they score orders: a host
  * framework whose memory pool owns the device and forbids outside allocations, a
@@ -229,6 +236,9 @@ int bn_chains_step_profiled(bn_chains* c, int64_t steps, void* stream, double* s
 #define BN_OUT_RECORD_LEN   14 /* 1 int64: states recorded so far per chain              */
 #define BN_OUT_ITEMS        15 /* 1 int64: (node, chain) items re-scored so far (every
                                   step re-scores the nodes between the swapped positions) */
+#define BN_OUT_LOGITS       16 /* chains x n(n-1)/2 float32: the proposal network's logits
+                                  on each chain's current order, as the learned proposal
+                                  on a pruned table holds them (BN_EINVAL otherwise)    */
 int bn_chains_read(const bn_chains* c, int what, void* out, int mem, void* stream);
 
 void bn_chains_free(bn_chains* c);
@@ -319,8 +329,15 @@ void bn_mlp_free(bn_mlp* m);
  *                        - ln q(pair | sigma)  (the reverse move swaps the same pair)
  *   BN_PROPOSAL_TRAIN    uniform swaps; after every step the network takes one Adam step
  *                        on that step's proposals (sigma, pair, alpha = min(1, 10^delta))
- * Random numbers of the learned draw: u = ((x2 >> 11) + 0.5) 2^-53 of the step's Philox
- * block, inverted through the cumulative q in pair order.  m must have the chains' n and
+ * Random numbers of the learned draw, from the step's Philox block: on a pruned table
+ * (bn_table_set_scan) the mixture component is drawn first, uniform iff
+ * ((x3 >> 11) + 0.5) 2^-53 < eps_mix (pair = floor(x0 P / 2^64)), else the softmax pair is
+ * inverted from u = ((x2 >> 11) + 0.5) 2^-53 through the cumulative softmax, tile of 32
+ * pairs first; on a full table u inverts the cumulative mixture q in pair order.  On a
+ * pruned table the network's first layer is evaluated as a sum of per-(position, node)
+ * rows held in 32-bit fixed point (scale 2^-s, s <= 24 chosen so no sum can overflow),
+ * so q(. | sigma) depends on sigma alone; the network is read when this call is made
+ * (later training needs another call).  m must have the chains' n and
  * batch_cap >= chains; it must outlive the chains (or the next call here).  eps_mix in
  * (0, 1] keeps every pair proposable.  Errors: BN_EINVAL, BN_ENOMEM, BN_ECUDA. */
 #define BN_PROPOSAL_UNIFORM 0

@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 MEM_HOST, MEM_DEVICE = 0, 1
 OUT = dict(orders=1, scores=2, ranks=3, best_orders=4, best_scores=5, best_ranks=6,
            edge_counts=7, accepts=8, trace_score=9, trace_accept=10, steps=11, ess=12, record=13,
-           record_len=14, items=15)
+           record_len=14, items=15, logits=16)
 
 # names the ABI exports (include/bn.h); tests check the library against this list
 ABI = ["bn_build_scores", "bn_table_from_scores", "bn_table_info", "bn_table_scores",
@@ -77,6 +77,7 @@ def _load():
     _L.bn_table_free.restype = None
     _L.bn_score_orders.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp]
     _L.bn_score_orders_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
+    _L.bn_score_orders_profiled.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp, C.POINTER(C.c_double)]
     _L.bn_unrank.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_uint64)]
     _L.bn_rank.argtypes = [C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_int64)]
     _L.bn_chains_create.argtypes = [_vp, C.POINTER(MCMCParams), _vp, C.c_int, _vp, C.POINTER(_vp)]
@@ -271,6 +272,21 @@ def score_orders(t: Table, orders):
     return br, sc
 
 
+def score_orders_profiled(t: Table, orders):
+    """score_orders on device tensors with the scan kernel's device time (ms, CUDA events
+    around its launch): (best_rank, score, scan_ms)."""
+    import torch
+    n = table_info(t)["n"]
+    o = _dev(orders, torch.uint8)
+    B = o.shape[0]
+    br = torch.empty((B, n), dtype=torch.int32, device=o.device)
+    sc = torch.empty((B,), dtype=torch.float64, device=o.device)
+    ms = C.c_double()
+    _check(lib().bn_score_orders_profiled(t.handle, _ptr(o), B, _ptr(br), _ptr(sc), MEM_DEVICE, _stream(o),
+                                          C.byref(ms)))
+    return br, sc, ms.value
+
+
 SCAN_FULL, SCAN_PRUNED = 0, 1
 
 
@@ -361,12 +377,13 @@ _OUT_SHAPES = {
     "accepts": (np.int64, "c"), "trace_score": (np.float64, "ct"),
     "trace_accept": (np.uint8, "ct"), "steps": (np.int64, "1"), "ess": (np.float64, "nn"),
     "record": (np.uint64, "cnnw"), "record_len": (np.int64, "1"), "items": (np.int64, "1"),
+    "logits": (np.float32, "cP"),
 }
 
 
 def chains_read(c: Chains, what: str):
     dtype, dims = _OUT_SHAPES[what]
-    size = {"c": c.params.chains, "n": c.n, "t": c.params.trace_cap, "1": 1,
+    size = {"c": c.params.chains, "n": c.n, "t": c.params.trace_cap, "1": 1, "P": c.n * (c.n - 1) // 2,
             "w": max(1, (c.params.record_cap + 63) // 64) if c.params.record_every > 0 else 0}
     shape = tuple(size[d] for d in dims)
     out = np.empty(shape, dtype)

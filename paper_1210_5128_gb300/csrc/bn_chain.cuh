@@ -1,0 +1,120 @@
+// bn_chain.cuh -- device state of a set of MH chains over node orders, shared by the
+// uniform-proposal sampler (bn_mcmc.cu) and the learned-proposal sampler (bn_learned.cu).
+#pragma once
+
+#include "bn_mlp.cuh"
+#include "bn_table.cuh"
+
+namespace bn {
+
+static constexpr double LN10 = 2.302585092994045684017991454684364208;
+
+struct ChainState {
+    int n, C;
+    uint64_t seed;
+    int64_t burn_in;
+    int literal_log;
+    int64_t trace_cap;
+    int record_every, record_cap, rec_words;
+    const int64_t* keys;       // table
+    const uint64_t* pst;
+    const uint32_t* srank;
+    int64_t Sp;
+    uint8_t* cur_order;        // C*n
+    uint32_t* cur_rank;        // C*n
+    int64_t* cur_key;          // C*n
+    double* cur_score;         // C
+    uint8_t* best_order;
+    uint32_t* best_rank;
+    double* best_score;
+    int64_t* accepts;
+    uint32_t* edge;            // C*n*n
+    uint8_t* prop_order;       // C*n
+    uint8_t* prop_ab;          // C*2
+    double* prop_u;            // C
+    uint32_t* list_count;      // n
+    uint64_t* list_pc;         // n*C
+    uint32_t* slot_of;         // C*n
+    uint32_t* list_best;       // n*C  scan results (sorted positions)
+    int64_t* step;             // 1
+    uint32_t* status;          // 1
+    uint32_t* done;            // 1
+    double* trace_score;       // C*trace_cap
+    uint8_t* trace_accept;
+    uint64_t* rec_bits;        // C*n*n*rec_words
+    int64_t* rec_count;        // 1
+    int64_t* items_total;      // 1  (node, chain) items scanned so far
+    // proposal (BN_PROPOSAL_*): learned draws and their log proposal probabilities
+    int mode;
+    int P;                     // n(n-1)/2
+    float eps_mix;
+    float* cur_lq;             // C*P  log q(. | current order)
+    float* prop_lq;            // C*P  log q(. | proposed order)
+    uint32_t* prop_pair;       // C
+    float* prop_lqf;           // C  log q(pair | current)
+    float* delta;              // C  s' - s of the last step (training target)
+    uint8_t* changed;          // C  1 if the last proposal changed some node's parent set
+    uint8_t* train_orders;     // C*n  pre-step orders of the last step
+    uint32_t* train_pairs;     // C
+    float* train_alpha;        // C
+};
+
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+__device__ __forceinline__ uint64_t compress_pred(uint64_t pred, int i)
+{
+    uint64_t lowm = (i == 0) ? 0ull : ((1ull << i) - 1);
+    return (pred & lowm) | ((i + 1 < 64) ? ((pred >> (i + 1)) << i) : 0ull);
+}
+
+// credit the post-burn-in steps [from, to) during which node v held parent set `rank`
+__device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, uint32_t rank, int64_t from, int64_t to)
+{
+    const int64_t lo = max(from, S.burn_in);
+    if (to <= lo) return;
+    const uint32_t d = (uint32_t)(to - lo);
+    uint64_t m = S.pst[rank];
+    uint32_t* E = S.edge + ((size_t)c * S.n + v) * S.n;
+    while (m) {
+        const int slot = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        atomicAdd(&E[slot + (slot >= v ? 1 : 0)], d);     // no read-back: the warp does not wait
+    }
+}
+
+// rounding bound of the MH test's right-hand side: two sequential sums of n entries of
+// magnitude <= max_abs (each within (n - 1) 2^-53 n max_abs) and the change summed over
+// the re-scored nodes, times ln 10, with a factor 8 to spare
+inline double mh_margin(int n, double max_abs)
+{
+    return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52;
+}
+
+struct LearnedPath;                       // bn_learned.cu
+int learned_setup(::bn_chains* ch, cudaStream_t s);
+int learned_step(::bn_chains* ch, int64_t steps, cudaStream_t s);
+void learned_free(LearnedPath* lp);
+// the path's network outputs (and with `weights` its copies of the network) are stale
+void learned_invalidate(LearnedPath* lp, bool weights);
+bool learned_path(const ::bn_chains* ch);
+int learned_read_logits(const ::bn_chains* ch, float* out, int mem, cudaStream_t s);
+
+}  // namespace bn
+
+struct bn_chains {
+    const bn_table* t = nullptr;
+    bn_mcmc_params p{};
+    bn::ChainState S{};
+    bn::ScanPlan plan{};
+    void* block = nullptr;          // one device allocation holding all state
+    void* prop_block = nullptr;     // learned-proposal buffers (bn_chains_set_proposal)
+    bn_mlp* mlp = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int exec_scan_mode = -1;        // table scan mode the graph was captured with
+    int per_sweep = 3;              // kernel launches per step
+    int64_t steps = 0;
+    int dev = 0;
+    bn::LearnedPath* lp = nullptr;  // fast learned-proposal path (bn_learned.cu)
+    bool lq_valid = false;          // S.cur_lq matches the current orders (graph path)
+};
+

@@ -17,70 +17,9 @@
 #include <cstring>
 #include <vector>
 
-#include "bn_mlp.cuh"
-#include "bn_table.cuh"
+#include "bn_chain.cuh"
 
 namespace bn {
-
-static constexpr double LN10 = 2.302585092994045684017991454684364208;
-
-struct ChainState {
-    int n, C;
-    uint64_t seed;
-    int64_t burn_in;
-    int literal_log;
-    int64_t trace_cap;
-    int record_every, record_cap, rec_words;
-    const int64_t* keys;       // table
-    const uint64_t* pst;
-    const uint32_t* srank;
-    int64_t Sp;
-    uint8_t* cur_order;        // C*n
-    uint32_t* cur_rank;        // C*n
-    int64_t* cur_key;          // C*n
-    double* cur_score;         // C
-    uint8_t* best_order;
-    uint32_t* best_rank;
-    double* best_score;
-    int64_t* accepts;
-    uint32_t* edge;            // C*n*n
-    uint8_t* prop_order;       // C*n
-    uint8_t* prop_ab;          // C*2
-    double* prop_u;            // C
-    uint32_t* list_count;      // n
-    uint64_t* list_pc;         // n*C
-    uint32_t* slot_of;         // C*n
-    uint32_t* list_best;       // n*C  scan results (sorted positions)
-    int64_t* step;             // 1
-    uint32_t* status;          // 1
-    uint32_t* done;            // 1
-    double* trace_score;       // C*trace_cap
-    uint8_t* trace_accept;
-    uint64_t* rec_bits;        // C*n*n*rec_words
-    int64_t* rec_count;        // 1
-    int64_t* items_total;      // 1  (node, chain) items scanned so far
-    // proposal (BN_PROPOSAL_*): learned draws and their log proposal probabilities
-    int mode;
-    int P;                     // n(n-1)/2
-    float eps_mix;
-    float* cur_lq;             // C*P  log q(. | current order)
-    float* prop_lq;            // C*P  log q(. | proposed order)
-    uint32_t* prop_pair;       // C
-    float* prop_lqf;           // C  log q(pair | current)
-    float* delta;              // C  s' - s of the last step (training target)
-    uint8_t* changed;          // C  1 if the last proposal changed some node's parent set
-    uint8_t* train_orders;     // C*n  pre-step orders of the last step
-    uint32_t* train_pairs;     // C
-    float* train_alpha;        // C
-};
-
-__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
-
-__device__ __forceinline__ uint64_t compress_pred(uint64_t pred, int i)
-{
-    uint64_t lowm = (i == 0) ? 0ull : ((1ull << i) - 1);
-    return (pred & lowm) | ((i + 1 < 64) ? ((pred >> (i + 1)) << i) : 0ull);
-}
 
 // initial orders: Fisher-Yates from the identity driven by the Philox init stream
 __global__ void k_init_orders(ChainState S)
@@ -336,14 +275,6 @@ struct FusedArgs {
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
 };
 
-// rounding bound of the MH test's right-hand side: two sequential sums of n entries of
-// magnitude <= max_abs (each within (n - 1) 2^-53 n max_abs) and the change summed over
-// the re-scored nodes, times ln 10, with a factor 8 to spare
-static double mh_margin(int n, double max_abs)
-{
-    return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52;
-}
-
 // per-warp shared-memory cache of a network's survivors: candidate mask, rank and key of
 // every survivor, and the node offsets
 __host__ __device__ constexpr size_t surv_cache_bytes(int cap)
@@ -354,26 +285,14 @@ static constexpr int SURV_CAP_MAX = 2400;
 
 static constexpr int FUSED_WARPS = 2;
 
-__device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, uint32_t rank, int64_t from, int64_t to)
-{
-    const int64_t lo = max(from, S.burn_in);
-    if (to <= lo) return;
-    const uint32_t d = (uint32_t)(to - lo);
-    uint64_t m = S.pst[rank];
-    uint32_t* E = S.edge + ((size_t)c * S.n + v) * S.n;
-    while (m) {
-        const int slot = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        E[slot + (slot >= v ? 1 : 0)] += d;
-    }
-}
-
 struct FusedSmem {
     uint8_t ord[MAXN];
     uint32_t rank[MAXN];
     int64_t key[MAXN];
     int64_t nkey[MAXN];
     int64_t since[MAXN];
+    uint64_t pre[MAXN];        // nodes at positions < p of the current order
+    uint64_t rx0[32], rx1[32]; // Philox outputs x0, x1 of the next 32 steps
 };
 
 __device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
@@ -405,28 +324,12 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         W.key[i] = S.cur_key[(size_t)c * n + i];
         W.since[i] = F.t0;
     }
-    double score = S.cur_score[c], best = S.best_score[c];
-    int64_t acc_count = 0, items = 0;
     __syncwarp();
-    for (int it = 0; it < F.iters; ++it) {
-        const int64_t t = F.t0 + it;
-        const U64x4 x = philox4x64((uint64_t)t, (uint64_t)c, 0, 0, S.seed, 0);
-        int a, b;
-        pair_decode(n, __umul64hi(x.x[0], P), a, b);
-        // proposed order on the lanes (positions lane, lane + 32) and prefix masks
-        int v[2];
-        uint64_t bit[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = lane + 32 * h;
-            v[h] = 0;
-            bit[h] = 0;
-            if (p < n) {
-                v[h] = W.ord[(p == a) ? b : (p == b) ? a : p];
-                bit[h] = 1ull << v[h];
-            }
-        }
-        uint64_t s0 = bit[0], s1 = bit[1];
+    {
+        // prefix masks of the current order (positions lane, lane + 32): exclusive OR-scan
+        uint64_t b0 = lane < n ? 1ull << W.ord[lane] : 0ull;
+        uint64_t b1 = lane + 32 < n ? 1ull << W.ord[lane + 32] : 0ull;
+        uint64_t s0 = b0, s1 = b1;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint64_t t0 = __shfl_up_sync(0xffffffffu, s0, off);
@@ -434,95 +337,134 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             if (lane >= off) { s0 |= t0; s1 |= t1; }
         }
         const uint64_t first_half = __shfl_sync(0xffffffffu, s0, 31);
+        if (lane < n) W.pre[lane] = s0 & ~b0;
+        if (lane + 32 < n) W.pre[lane + 32] = (s1 | first_half) & ~b1;
+    }
+    double score = S.cur_score[c], best = S.best_score[c];
+    int64_t acc_count = 0, items = 0;
+    __syncwarp();
+    for (int it = 0; it < F.iters; ++it) {
+        const int64_t t = F.t0 + it;
+        if ((it & 31) == 0) {
+            // the next 32 steps' Philox blocks, one per lane
+            const U64x4 xr = philox4x64((uint64_t)(t + lane), (uint64_t)c, 0, 0, S.seed, 0);
+            W.rx0[lane] = xr.x[0];
+            W.rx1[lane] = xr.x[1];
+            __syncwarp();
+        }
+        const uint64_t x0 = W.rx0[it & 31], x1 = W.rx1[it & 31];
+        int a, b;
+        pair_decode(n, __umul64hi(x0, P), a, b);
+        const int va = W.ord[a], vb = W.ord[b];
+        const uint64_t bva = 1ull << va, bvb = 1ull << vb;
+        // the span a..b of the proposed order: its nodes and their predecessor sets (the
+        // current prefix with node va replaced by vb between a and b)
+        int node[2] = {-1, -1};
         uint32_t nrank[2] = {0, 0};
-        // keys of the proposal: unaffected nodes keep theirs, the span a..b is re-scored
-        for (int i = lane; i < n; i += 32) W.nkey[i] = W.key[i];
-        __syncwarp();
+        bool moved = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int p = lane + 32 * h;
             if (p < n && p >= a && p <= b) {
-                const int node = v[h];
-                const uint64_t excl = (h == 0 ? s0 : (s1 | first_half)) & ~bit[h];
-                const uint64_t npc = ~compress_pred(excl, node);
+                const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
+                const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
+                const uint64_t npc = ~compress_pred(excl, nd);
                 if (F.staged) {
                     // survivors of the node in score order: the first consistent one wins
-                    const uint32_t j1 = c_off[node + 1];
-                    uint32_t j = c_off[node];
+                    const uint32_t j1 = c_off[nd + 1];
+                    uint32_t j = c_off[nd];
                     while (j + 1 < j1 && (c_mask[j] & npc) != 0ull) ++j;
                     nrank[h] = c_rank[j];
-                    W.nkey[node] = c_key[j];
+                    W.nkey[nd] = c_key[j];
                 } else {
-                    const uint64_t* M = F.amask + F.aoff[node];
-                    const uint32_t cnt = F.acnt[node];
+                    const uint64_t* M = F.amask + F.aoff[nd];
+                    const uint32_t cnt = F.acnt[nd];
                     uint32_t sp = 0;
                     for (uint32_t j = 0; j < cnt; ++j) {
-                        if ((M[j] & npc) == 0ull) { sp = F.aspos[F.aoff[node] + j]; break; }
+                        if ((M[j] & npc) == 0ull) { sp = F.aspos[F.aoff[nd] + j]; break; }
                     }
-                    nrank[h] = S.srank[(size_t)node * S.Sp + sp];
-                    W.nkey[node] = S.keys[(size_t)node * S.Sp + nrank[h]];
+                    nrank[h] = S.srank[(size_t)nd * S.Sp + sp];
+                    W.nkey[nd] = S.keys[(size_t)nd * S.Sp + nrank[h]];
                 }
+                node[h] = nd;
+                moved |= nrank[h] != W.rank[nd];
             }
         }
-        __syncwarp();
-        // MH test.  The exact test compares ln u with ln10 (s' - s), s' the FP64 sum over
-        // nodes in ascending id.  Most steps are decided without it: the change of the
-        // re-scored nodes alone (any summation order) is within ~n eps sum|entries| of
-        // s' - s and an FP32 log(u) within 1e-6 (1 + |ln u|) of ln u; when the two sides
-        // are farther apart than both errors the decision is the exact one.  Close calls
-        // and accepted moves (whose new score the state keeps) take the exact path.
-        double dpart = 0.0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = lane + 32 * h;
-            if (p < n && p >= a && p <= b)
-                dpart += key_to_double(W.nkey[v[h]]) - key_to_double(W.key[v[h]]);
-        }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
-        int acc = 0;
-        double s2 = 0.0;
-        if (lane == 0) {
-            const double u = __dmul_rn(__dadd_rn((double)(x.x[1] >> 12), 0.5), 0x1p-52);
-            const float luf = logf((float)u);
-            const double xa = S.literal_log ? dpart : LN10 * dpart;
-            const double margin = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
-            const double gap = (double)luf - xa;
-            int exact = 0;
-            if (gap > margin) acc = 0;
-            else if (gap < -margin) { acc = 1; exact = 1; }
-            else exact = 2;
-            if (exact) {
-                for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
-                if (exact == 2) {
-                    const double delta = __dsub_rn(s2, score);
-                    const double lu = log(u);
-                    acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
-                }
-            }
-        }
-        acc = __shfl_sync(0xffffffffu, acc, 0);
-        s2 = __shfl_sync(0xffffffffu, s2, 0);
+        moved = __any_sync(0xffffffffu, moved);
         items += b - a + 1;
+        int acc = 1;
+        double s2 = score;
+        if (moved) {
+            __syncwarp();
+            // MH test.  The exact test compares ln u with ln10 (s' - s), s' the FP64 sum over
+            // nodes in ascending id.  Most steps are decided without it: the change of the
+            // re-scored nodes alone (any summation order) is within ~n eps sum|entries| of
+            // s' - s and an FP32 log(u) within 1e-6 (1 + |ln u|) of ln u; when the two sides
+            // are farther apart than both errors the decision is the exact one.  Close calls
+            // and accepted moves (whose new score the state keeps) take the exact path.
+            double dpart = 0.0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (node[h] >= 0) dpart += key_to_double(W.nkey[node[h]]) - key_to_double(W.key[node[h]]);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
+            // nodes of the span (their keys are in nkey)
+            uint64_t span = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (node[h] >= 0) span |= 1ull << node[h];
+            const uint32_t span_lo = __reduce_or_sync(0xffffffffu, (uint32_t)span);
+            const uint32_t span_hi = __reduce_or_sync(0xffffffffu, (uint32_t)(span >> 32));
+            const uint64_t spanm = ((uint64_t)span_hi << 32) | span_lo;
+            acc = 0;
+            if (lane == 0) {
+                const double u = __dmul_rn(__dadd_rn((double)(x1 >> 12), 0.5), 0x1p-52);
+                const float luf = logf((float)u);
+                const double xa = S.literal_log ? dpart : LN10 * dpart;
+                const double margin = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
+                const double gap = (double)luf - xa;
+                int exact = 0;
+                if (gap > margin) acc = 0;
+                else if (gap < -margin) { acc = 1; exact = 1; }
+                else exact = 2;
+                if (exact) {
+                    s2 = 0.0;
+                    for (int i = 0; i < n; ++i)
+                        s2 = __dadd_rn(s2, key_to_double(((spanm >> i) & 1) ? W.nkey[i] : W.key[i]));
+                    if (exact == 2) {
+                        const double delta = __dsub_rn(s2, score);
+                        const double lu = log(u);
+                        acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+                    }
+                }
+            }
+            acc = __shfl_sync(0xffffffffu, acc, 0);
+            s2 = __shfl_sync(0xffffffffu, s2, 0);
+        }
+        // (not moved: no parent set changes, s' = s bit for bit and ln u < 0 accepts)
         if (acc) {
+            if (moved) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int nd = node[h];
+                    if (nd >= 0 && nrank[h] != W.rank[nd]) {
+                        credit_edges(S, c, nd, W.rank[nd], W.since[nd], t);
+                        W.since[nd] = t;
+                        W.rank[nd] = nrank[h];
+                        W.key[nd] = W.nkey[nd];
+                    }
+                }
+            }
+            // prefixes of positions a+1..b now hold vb instead of va
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int p = lane + 32 * h;
-                if (p < n && p >= a && p <= b) {
-                    const int node = v[h];
-                    if (nrank[h] != W.rank[node]) {
-                        credit_edges(S, c, node, W.rank[node], W.since[node], t);
-                        W.since[node] = t;
-                        W.rank[node] = nrank[h];
-                    }
-                    W.key[node] = W.nkey[node];
-                }
+                if (p < n && p > a && p <= b) W.pre[p] = (W.pre[p] & ~bva) | bvb;
             }
             __syncwarp();
             if (lane == 0) {
-                const uint8_t oa = W.ord[a];
-                W.ord[a] = W.ord[b];
-                W.ord[b] = oa;
+                W.ord[a] = (uint8_t)vb;
+                W.ord[b] = (uint8_t)va;
             }
             __syncwarp();
             score = s2;
@@ -548,7 +490,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     const int slot = __ffsll((long long)m) - 1;
                     m &= m - 1;
                     const int par = slot + (slot >= i ? 1 : 0);
-                    S.rec_bits[(((size_t)c * n + i) * n + par) * S.rec_words + (ridx >> 6)] |= 1ull << (ridx & 63);
+                    atomicOr((unsigned long long*)&S.rec_bits[(((size_t)c * n + i) * n + par) * S.rec_words + (ridx >> 6)],
+                             1ull << (ridx & 63));
                 }
             }
         }
@@ -838,21 +781,6 @@ __global__ void k_pick_best(const double* __restrict__ best_score, const uint8_t
 
 using namespace bn;
 
-struct bn_chains {
-    const bn_table* t = nullptr;
-    bn_mcmc_params p{};
-    ChainState S{};
-    ScanPlan plan{};
-    void* block = nullptr;          // one device allocation holding all state
-    void* prop_block = nullptr;     // learned-proposal buffers (bn_chains_set_proposal)
-    bn_mlp* mlp = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int exec_scan_mode = -1;        // table scan mode the graph was captured with
-    int per_sweep = 3;              // kernel launches per step
-    int64_t steps = 0;
-    int dev = 0;
-};
-
 static constexpr int FUSED_ITERS = 256;     // MH steps per fused launch
 
 static bool fused_path(const bn_chains* ch)
@@ -915,6 +843,18 @@ static int sweep_launch(bn_chains* ch, cudaStream_t s, cudaEvent_t ev0 = nullptr
         if ((rc = mlp_adam_dev(ch->mlp, s))) return rc;
     }
     ch->per_sweep = (int)(bn_kernel_launches() - l0);
+    return BN_OK;
+}
+
+// q(. | current order) of every chain for the graph path of the learned proposal
+static int refresh_lq(bn_chains* ch, cudaStream_t s)
+{
+    ChainState& S = ch->S;
+    int rc = mlp_forward_dev(ch->mlp, S.cur_order, S.C, false, s);
+    if (rc) return rc;
+    k_log_q<<<(S.C + 7) / 8, 256, 0, s>>>(ch->mlp->L, ch->mlp->Pp, S.C, S.P, S.eps_mix, S.cur_lq);
+    BN_LAUNCH_CHECK("k_log_q");
+    ch->lq_valid = true;
     return BN_OK;
 }
 
@@ -1055,6 +995,18 @@ extern "C" int bn_chains_step(bn_chains* ch, int64_t steps, void* stream)
             if (s) cudaStreamDestroy(s);
         }
     } own_guard{own};
+    if (learned_path(ch)) {
+        int rc = learned_step(ch, steps, s);
+        if (rc) return rc;
+        ch->steps += steps;
+        ch->lq_valid = false;
+        return BN_OK;
+    }
+    learned_invalidate(ch->lp, false);         // the orders move outside the learned path
+    if (ch->S.mode == BN_PROPOSAL_LEARNED && !ch->lq_valid) {
+        int rc = refresh_lq(ch, s);
+        if (rc) return rc;
+    }
     if (fused_path(ch)) {
         for (int64_t done = 0; done < steps;) {
             const int it = (int)std::min<int64_t>(FUSED_ITERS, steps - done);
@@ -1103,7 +1055,7 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
     if (!ch) return set_error(BN_EINVAL, "bn_chains_step_profiled: NULL chains");
     if (steps < 0) return set_error(BN_EINVAL, "bn_chains_step_profiled: steps < 0");
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<cudaEvent_t> ev(2 * (size_t)steps);
+    std::vector<cudaEvent_t> ev(2 * (size_t)std::max<int64_t>(steps, 1));
     for (auto& e : ev) BN_CUDA(cudaEventCreate(&e));
     struct Ev {
         std::vector<cudaEvent_t>& v;
@@ -1113,7 +1065,15 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
         }
     } ev_guard{ev};
     int64_t launches = steps;
-    if (fused_path(ch)) {
+    if (learned_path(ch)) {
+        // the whole learned step (three kernels per MH step) between one pair of events
+        BN_CUDA(cudaEventRecord(ev[0], s));
+        int rc = learned_step(ch, steps, s);
+        if (rc) return rc;
+        BN_CUDA(cudaEventRecord(ev[1], s));
+        ch->lq_valid = false;
+        launches = 1;
+    } else if (fused_path(ch)) {
         // the fused kernel is the whole step: its launches are what the events bracket
         launches = 0;
         for (int64_t done = 0; done < steps; ++launches) {
@@ -1123,6 +1083,11 @@ extern "C" int bn_chains_step_profiled(bn_chains* ch, int64_t steps, void* strea
             done += it;
         }
     } else {
+        learned_invalidate(ch->lp, false);
+        if (ch->S.mode == BN_PROPOSAL_LEARNED && !ch->lq_valid) {
+            int rc = refresh_lq(ch, s);
+            if (rc) return rc;
+        }
         for (int64_t i = 0; i < steps; ++i) {
             int rc = sweep_launch(ch, s, ev[2 * i], ev[2 * i + 1]);
             if (rc) return rc;
@@ -1189,6 +1154,7 @@ extern "C" int bn_chains_read(const bn_chains* ch, int what, void* out, int mem,
             BN_CUDA(cudaStreamSynchronize(s));
             return BN_OK;
         }
+        case BN_OUT_LOGITS: return learned_read_logits(ch, (float*)out, mem, s);
         default: return set_error(BN_EINVAL, "bn_chains_read: unknown output %d", what);
     }
     if (bytes) BN_CUDA(cudaMemcpyAsync(out, src, bytes, mem == BN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
@@ -1200,6 +1166,7 @@ extern "C" void bn_chains_free(bn_chains* ch)
 {
     if (!ch) return;
     if (ch->exec) cudaGraphExecDestroy(ch->exec);
+    learned_free(ch->lp);
     cudaFree(ch->block);
     cudaFree(ch->prop_block);
     delete ch;
@@ -1256,12 +1223,12 @@ extern "C" int bn_chains_set_proposal(bn_chains* ch, bn_mlp* m, int mode, double
     ch->mlp = m;
     S.mode = mode;
     S.eps_mix = (float)eps_mix;
+    learned_invalidate(ch->lp, true);                 // network or proposal changed
+    ch->lq_valid = false;
     if (mode == BN_PROPOSAL_LEARNED) {
         // q(. | current order) of every chain from the network as it is now
-        int rc = mlp_forward_dev(m, S.cur_order, S.C, false, s);
+        int rc = learned_path(ch) ? learned_setup(ch, s) : refresh_lq(ch, s);
         if (rc) return rc;
-        k_log_q<<<(S.C + 7) / 8, 256, 0, s>>>(m->L, m->Pp, S.C, S.P, S.eps_mix, S.cur_lq);
-        BN_LAUNCH_CHECK("k_log_q");
     }
     uint32_t st = 0;
     BN_CUDA(cudaMemcpyAsync(&st, m ? m->status : S.status, 4, cudaMemcpyDeviceToHost, s));

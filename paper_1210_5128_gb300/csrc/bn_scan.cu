@@ -278,8 +278,24 @@ __global__ void k_reduce_orders(const uint32_t* __restrict__ list_best, const ui
 
 using namespace bn;
 
-extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
-                               double* order_score, int mem, void* stream)
+// the stream-ordered pool keeps freed scratch mapped (its default release threshold of 0
+// would unmap it at every synchronisation and map it again on the next call)
+static void keep_pool_mapped()
+{
+    static bool done[64] = {false};
+    const int d = device_id();
+    if (d < 0 || d >= 64 || done[d]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+        uint64_t thr = (uint64_t)256 << 20;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[d] = true;
+}
+
+static int score_orders_impl(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
+                             double* order_score, int mem, void* stream, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     set_error(BN_OK, "");
     if (!t) return set_error(BN_EINVAL, "bn_score_orders: NULL table");
@@ -290,6 +306,7 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
     cudaStream_t s = (cudaStream_t)stream;
     const int n = t->n;
     const ScanPlan pl = plan_scan(t, B);
+    keep_pool_mapped();
 
     // one scratch block: orders | list_pc | list_best | counts | status | ranks | scores
     size_t off = 0;
@@ -330,7 +347,9 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
     BN_CUDA(cudaMemsetAsync(d_st, 0, sizeof(uint32_t), s));
     int rc = launch_pred_lists(d_orders, B, n, d_pc, d_best, d_cnt, d_st, s);
     if (rc) return rc;
+    if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
     if ((rc = launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_st, s))) return rc;
+    if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, d_rank, d_score);
     BN_LAUNCH_CHECK("k_reduce_orders");
     if (mem == BN_MEM_HOST) {
@@ -344,6 +363,30 @@ extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, 
     if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_score_orders: an order is not a permutation of 0..n-1");
     if (st & STATUS_TIMEOUT) return set_error(BN_ETIMEOUT, "bn_score_orders: a bounded device wait expired");
     return BN_OK;
+}
+
+extern "C" int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
+                               double* order_score, int mem, void* stream)
+{
+    return score_orders_impl(t, orders, B, best_rank, order_score, mem, stream, nullptr, nullptr);
+}
+
+extern "C" int bn_score_orders_profiled(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
+                                        double* order_score, int mem, void* stream, double* scan_ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__);
+    }
+    int rc = score_orders_impl(t, orders, B, best_rank, order_score, mem, stream, e0, e1);
+    float ms = 0.f;
+    if (rc == BN_OK && B > 0 && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "cudaEventElapsedTime", __FILE__, __LINE__);
+    if (scan_ms) *scan_ms = (double)ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 extern "C" int bn_table_autotune(bn_table* t, int max_items, void* stream, int64_t* chosen)

@@ -29,7 +29,8 @@ def _exact_edge_posterior(tab, k):
     return post
 
 
-def test_learned_proposal_keeps_the_posterior_n6(gpu):
+@pytest.mark.parametrize("scan", ["full", "pruned"])
+def test_learned_proposal_keeps_the_posterior_n6(gpu, scan):
     data, arity, k, R, _ = synth.workload("n6_k2_m100", 7)
     # a flatter posterior (fewer samples) so several orders carry weight
     data = data[:30].copy()
@@ -41,6 +42,8 @@ def test_learned_proposal_keeps_the_posterior_n6(gpu):
     w["b3"] = np.linspace(-3, 3, n * (n - 1) // 2).astype(np.float32)
     net = gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=128)
     t = gpu.table_from_scores(tab, k)
+    if scan == "pruned":                  # the three-kernel learned step path
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
     C, steps, burn = 128, 6000, 500
     ch = gpu.chains_create(t, C, 99, burn_in=burn)
     gpu.chains_set_proposal(ch, net, gpu.PROPOSAL_LEARNED, eps_mix=0.2)
@@ -60,13 +63,16 @@ def test_learned_proposal_keeps_the_posterior_n6(gpu):
     assert np.abs(fu - exact).max() < 0.02
 
 
-def test_training_on_history_raises_the_rate_of_useful_moves_n20(gpu):
+@pytest.mark.parametrize("scan", ["full", "pruned"])
+def test_training_on_history_raises_the_rate_of_useful_moves_n20(gpu, scan):
     """The network is trained to propose swaps that are accepted AND change the graph
     (swaps that change no parent set are always accepted but move nothing).  After
     training, the fraction of steps whose order score actually changes must be higher
     with the learned proposal than with uniform swaps from the same states."""
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     t = gpu.build_scores(data, arity, k, R=R)
+    if scan == "pruned":
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
     n, d, H = 20, 32, 256
     net = gpu.mlp_create(n, synth.mlp_init_weights(n, d, H, 4), hidden=H, d=d, batch_cap=256, lr=2e-3)
     C, burn, train, m = 256, 200, 600, 300
