@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--ess-thin", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-ess", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven 96-network batch")
+    ap.add_argument("--batch-iters", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -290,6 +292,26 @@ def main():
     S = bn.table_info(table)["sets_per_node"]
     seed = 0xC0FFEE + 7919 * rank
 
+    # ---- bn_score_orders on a few orders: the full-table scan at memory speed -------------
+    #      (the paper scores one order per MH iteration); device time of the scan kernel by
+    #      CUDA events around its launch, L2 flushed before every call
+    hbm_leg = []
+    flush_hbm = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    hbm_bytes = 4 * n * S + 8 * S            # sorted positions of every entry + the mask table once
+    for B in (1, 2, 4):
+        orders = torch.from_numpy(synth.random_orders(n, B, 100 + B)).to(dev)
+        for _ in range(3):
+            bn.score_orders_profiled(table, orders)
+        tot = 0.0
+        for _ in range(10):
+            flush_hbm.add_(1)
+            torch.cuda.synchronize()
+            tot += bn.score_orders_profiled(table, orders)[2]
+        us = 1000.0 * tot / 10
+        hbm_leg.append({"orders": B, "scan_us": us, "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
+                        "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak})
+    del flush_hbm
+
     with torch.cuda.stream(stream):
         # ---- full-table scan sampler ----------------------------------------------------
         full = bn.chains_create(table, args.chains, seed=seed)
@@ -357,6 +379,42 @@ def main():
                "learned_over_plain_ess_per_s": (learned["ess_per_s"] / plain["ess_per_s"])
                if learned["ess_per_s"] and plain["ess_per_s"] else None}
 
+    # ---- uneven batch: 96 networks (n 10..60, arity 2..4, m 200..5000, k 3..4), 32 chains
+    #      each, every network's chains in one fused launch --------------------------------
+    batch = None
+    if not args.no_batch and rank == 0:
+        nets = synth.uneven_batch(96, 0xB4E50000 + 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tabs = [bn.build_scores(d_, a_, k_, R=r_) for d_, a_, k_, r_, _ in nets]
+        torch.cuda.synchronize()
+        b_build = time.perf_counter() - t0
+        b_entries = sum(bn.table_info(tb)["n"] * bn.table_info(tb)["sets_per_node"] for tb in tabs)
+        for tb in tabs:
+            bn.table_set_scan(tb, bn.SCAN_PRUNED)
+        bat = bn.batch_create(tabs, 32, seed + 5)
+        bat.step(256)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bat.step(args.batch_iters)
+        e1.record()
+        torch.cuda.synchronize()
+        b_ms = e0.elapsed_time(e1)
+        b_chains = 96 * 32
+        batch = {"networks": 96, "chains_per_network": 32, "iterations": args.batch_iters,
+                 "order_evals_per_s": b_chains * args.batch_iters / (b_ms / 1000.0), "ms": b_ms,
+                 "n_range": [min(d_.shape[1] for d_, *_ in nets), max(d_.shape[1] for d_, *_ in nets)],
+                 "table_entries": int(b_entries), "table_build_s": b_build,
+                 "table_entries_per_s": b_entries / b_build,
+                 "note": "uniform-swap chains of every network in one fused launch per 256 steps "
+                         "(bn_batch_step); the learned proposal runs per network (bn_chains_set_proposal)"}
+        bat.free()
+        for tb in tabs:
+            tb.free()
+        del tabs
+
     # ---- end to end through the public C ABI with host buffers ----------------------------
     e2e_steps = max(50, args.steps) * args.iters_per_step
     e2e_calls = 2
@@ -405,6 +463,10 @@ def main():
                             f"steps x {args.chains} chains + results to host"},
             "gpu_launches": int(launches),
             "roofline": roof_full,
+            "roofline_hbm": {"kernel": "k_scan_nodes (bn_score_orders, full table, a few orders)", "bound": "hbm",
+                             "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                             "frac": hbm_leg[0]["frac"], "traffic": None, "peak_source": peak_src,
+                             "bytes_algorithmic": hbm_bytes, "by_orders": hbm_leg},
             "pruned_step": {"kernel": "k_chain_fused (256 MH iterations per launch, one warp per chain)",
                             "avg_ms_per_launch": avg_fused, "launches": fused_l,
                             "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
@@ -414,6 +476,7 @@ def main():
             "full_scan": {"value": world * args.chains * args.steps / (ms_full / 1000.0),
                           "ms_per_step": ms_full / args.steps, "items_per_step": items_full / args.steps},
             "ess": ess,
+            "uneven_batch": batch,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "table_build_s": build_s,

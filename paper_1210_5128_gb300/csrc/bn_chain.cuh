@@ -82,6 +82,23 @@ __device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, 
     }
 }
 
+// first survivor from j on (score order) whose parent set lies inside the predecessors
+// (npc = their complement): four independent loads per round; the node's last survivor,
+// the empty set, always qualifies, so no load passes j1 - 1
+__device__ __forceinline__ uint32_t first_consistent(const uint64_t* m, uint32_t j, uint32_t j1, uint64_t npc)
+{
+    while (j + 4 <= j1) {
+        const uint64_t a0 = m[j], a1 = m[j + 1], a2 = m[j + 2], a3 = m[j + 3];
+        if ((a0 & npc) == 0ull) return j;
+        if ((a1 & npc) == 0ull) return j + 1;
+        if ((a2 & npc) == 0ull) return j + 2;
+        if ((a3 & npc) == 0ull) return j + 3;
+        j += 4;
+    }
+    while (j + 1 < j1 && (m[j] & npc) != 0ull) ++j;
+    return j;
+}
+
 // rounding bound of the MH test's right-hand side: two sequential sums of n entries of
 // magnitude <= max_abs (each within (n - 1) 2^-53 n max_abs) and the change summed over
 // the re-scored nodes, times ln 10, with a factor 8 to spare

@@ -713,9 +713,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
                     const uint64_t npc = ~compress_pred(excl, nd);
                     // survivors in score order: the first consistent one wins (the empty
                     // set, always consistent, is the last survivor)
-                    const uint32_t j1 = soff[nd + 1];
-                    uint32_t j = soff[nd];
-                    while (j + 1 < j1 && (smask[j] & npc) != 0ull) ++j;
+                    const uint32_t j = first_consistent(smask, soff[nd], soff[nd + 1], npc);
                     const uint32_t r = srk[j];
                     const int64_t k = skey[j];
                     L.prank[(size_t)c * n + p] = r;

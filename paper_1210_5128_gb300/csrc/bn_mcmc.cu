@@ -283,7 +283,8 @@ __host__ __device__ constexpr size_t surv_cache_bytes(int cap)
 }
 static constexpr int SURV_CAP_MAX = 2400;
 
-static constexpr int FUSED_WARPS = 2;
+static constexpr int FUSED_WARPS = 2;      // chains per block of one network's fused launch
+static constexpr int BATCH_WARPS = 8;      // chains per block of a many-network launch
 
 struct FusedSmem {
     uint8_t ord[MAXN];
@@ -295,29 +296,44 @@ struct FusedSmem {
     uint64_t rx0[32], rx1[32]; // Philox outputs x0, x1 of the next 32 steps
 };
 
-__device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
-                                                 FusedSmem& W, uint8_t* cache)
+// a network's survivors (mask, rank, key in score order; node offsets) into the block's
+// shared-memory cache, by all `nthr` threads of the block
+__device__ __forceinline__ void fill_surv_cache(const ChainState& S, const FusedArgs& F, uint8_t* cache, int tid,
+                                                int nthr)
 {
     const int n = S.n;
-    const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
     uint64_t* c_mask = (uint64_t*)cache;
     int64_t* c_key = (int64_t*)(cache + 8 * (size_t)F.cap);
     uint32_t* c_rank = (uint32_t*)(cache + 16 * (size_t)F.cap);
     uint32_t* c_off = (uint32_t*)(cache + 20 * (size_t)F.cap);
-    if (F.staged) {
-        const uint32_t o0 = F.aoff[0];
-        for (int v = 0; v < n; ++v) {
-            const uint32_t ov = F.aoff[v], cv = F.acnt[v];
-            if (lane == 0) c_off[v] = ov - o0;
-            for (uint32_t j = lane; j < cv; j += 32) {
-                const uint32_t r = S.srank[(size_t)v * S.Sp + F.aspos[ov + j]];
-                c_mask[ov - o0 + j] = F.amask[ov + j];
-                c_rank[ov - o0 + j] = r;
-                c_key[ov - o0 + j] = S.keys[(size_t)v * S.Sp + r];
-            }
+    const uint32_t o0 = F.aoff[0];
+    const uint32_t total = F.aoff[n - 1] + F.acnt[n - 1] - o0;
+    for (uint32_t j = tid; j < total; j += nthr) {
+        // node of survivor j: offsets are ascending
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (F.aoff[mid] - o0 <= j) lo = mid;
+            else hi = mid;
         }
-        if (lane == 0) c_off[n] = F.aoff[n - 1] + F.acnt[n - 1] - o0;
+        const uint32_t r = S.srank[(size_t)lo * S.Sp + F.aspos[o0 + j]];
+        c_mask[j] = F.amask[o0 + j];
+        c_rank[j] = r;
+        c_key[j] = S.keys[(size_t)lo * S.Sp + r];
     }
+    for (int v = tid; v < n; v += nthr) c_off[v] = F.aoff[v] - o0;
+    if (tid == 0) c_off[n] = total;
+}
+
+__device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
+                                                 FusedSmem& W, const uint8_t* cache)
+{
+    const int n = S.n;
+    const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
+    const uint64_t* c_mask = (const uint64_t*)cache;
+    const int64_t* c_key = (const int64_t*)(cache + 8 * (size_t)F.cap);
+    const uint32_t* c_rank = (const uint32_t*)(cache + 16 * (size_t)F.cap);
+    const uint32_t* c_off = (const uint32_t*)(cache + 20 * (size_t)F.cap);
     for (int i = lane; i < n; i += 32) {
         W.ord[i] = S.cur_order[(size_t)c * n + i];
         W.rank[i] = S.cur_rank[(size_t)c * n + i];
@@ -342,6 +358,13 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     }
     double score = S.cur_score[c], best = S.best_score[c];
     int64_t acc_count = 0, items = 0;
+    // next recorded step and its index (recording: every record_every-th step from burn-in)
+    int64_t rec_next = INT64_MAX, rec_idx = 0;
+    if (S.record_every > 0) {
+        const int64_t from = F.t0 > S.burn_in ? F.t0 : S.burn_in;
+        rec_idx = (from - S.burn_in + S.record_every - 1) / S.record_every;
+        rec_next = rec_idx < S.record_cap ? S.burn_in + rec_idx * S.record_every : INT64_MAX;
+    }
     __syncwarp();
     for (int it = 0; it < F.iters; ++it) {
         const int64_t t = F.t0 + it;
@@ -371,9 +394,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 const uint64_t npc = ~compress_pred(excl, nd);
                 if (F.staged) {
                     // survivors of the node in score order: the first consistent one wins
-                    const uint32_t j1 = c_off[nd + 1];
-                    uint32_t j = c_off[nd];
-                    while (j + 1 < j1 && (c_mask[j] & npc) != 0ull) ++j;
+                    const uint32_t j = first_consistent(c_mask, c_off[nd], c_off[nd + 1], npc);
                     nrank[h] = c_rank[j];
                     W.nkey[nd] = c_key[j];
                 } else {
@@ -481,9 +502,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             S.trace_score[(size_t)c * S.trace_cap + t] = score;
             S.trace_accept[(size_t)c * S.trace_cap + t] = (uint8_t)acc;
         }
-        if (t >= S.burn_in && S.record_every > 0 && ((t - S.burn_in) % S.record_every) == 0 &&
-            (t - S.burn_in) / S.record_every < S.record_cap) {
-            const int64_t ridx = (t - S.burn_in) / S.record_every;
+        if (t == rec_next) {
+            const int64_t ridx = rec_idx;
             for (int i = lane; i < n; i += 32) {
                 uint64_t m = S.pst[W.rank[i]];
                 while (m) {
@@ -494,6 +514,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                              1ull << (ridx & 63));
                 }
             }
+            ++rec_idx;
+            rec_next = rec_idx < S.record_cap ? rec_next + S.record_every : INT64_MAX;
         }
         __syncwarp();
     }
@@ -517,48 +539,57 @@ __host__ __device__ constexpr size_t surv_cache_stride(int cap) { return (surv_c
 __global__ void __launch_bounds__(32 * FUSED_WARPS) k_chain_fused(ChainState S, FusedArgs F)
 {
     __shared__ FusedSmem sm[FUSED_WARPS];
-    extern __shared__ __align__(16) uint8_t fcache[];
+    extern __shared__ __align__(16) uint8_t fcache[];     // one survivor cache per block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * FUSED_WARPS + warp;
+    if (F.staged) {
+        fill_surv_cache(S, F, fcache, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
     if (c >= S.C) return;
-    chain_fused_body(S, F, c, lane, sm[warp], fcache + warp * surv_cache_stride(F.cap));
+    chain_fused_body(S, F, c, lane, sm[warp], fcache);
 }
 
-// many networks' chains in one launch: global warp g belongs to the network i with
-// base[i] <= g < base[i + 1] (chain g - base[i] of that network)
-__global__ void __launch_bounds__(32 * FUSED_WARPS) k_batch_fused(const ChainState* __restrict__ Ss,
+// many networks' chains in one launch: block g belongs to the network i with
+// cta_base[i] <= g < cta_base[i + 1]; its warps run chains (g - cta_base[i]) * BATCH_WARPS + warp
+// of that network, all sharing the block's copy of the network's survivors
+__global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainState* __restrict__ Ss,
                                                                  const FusedArgs* __restrict__ Fs,
-                                                                 const int64_t* __restrict__ base, int nnet)
+                                                                 const int64_t* __restrict__ cta_base, int nnet)
 {
-    __shared__ FusedSmem sm[FUSED_WARPS];
+    __shared__ FusedSmem sm[BATCH_WARPS];
     extern __shared__ __align__(16) uint8_t fcache[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * FUSED_WARPS + warp;
-    if (g >= base[nnet]) return;
+    const int64_t g = blockIdx.x;
+    if (g >= cta_base[nnet]) return;                                  // block-uniform
     int lo = 0, hi = nnet;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (base[mid] <= g) lo = mid;
+        if (cta_base[mid] <= g) lo = mid;
         else hi = mid;
     }
     const ChainState S = Ss[lo];
     const FusedArgs F = Fs[lo];
-    chain_fused_body(S, F, (int)(g - base[lo]), lane, sm[warp], fcache + warp * surv_cache_stride(F.cap));
+    if (F.staged) {
+        fill_surv_cache(S, F, fcache, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    const int64_t c = (g - cta_base[lo]) * BATCH_WARPS + warp;
+    if (c >= S.C) return;
+    chain_fused_body(S, F, (int)c, lane, sm[warp], fcache);
 }
 
-// the survivor cache of a launch: every network of it uses one layout (the largest that
-// fits); networks with more survivors walk them in global memory
 static int fused_smem_setup(int cap, size_t* smem)
 {
     static bool done[64] = {false};
     const int d = device_id();
-    const size_t mx = FUSED_WARPS * surv_cache_stride(SURV_CAP_MAX);
+    const size_t mx = surv_cache_stride(SURV_CAP_MAX);
     if (d < 64 && !done[d]) {
         BN_CUDA(cudaFuncSetAttribute(k_chain_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         done[d] = true;
     }
-    *smem = FUSED_WARPS * surv_cache_stride(cap);
+    *smem = surv_cache_stride(cap);
     return BN_OK;
 }
 
@@ -1335,21 +1366,17 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
     if (fused.empty()) return BN_OK;
     const int nf = (int)fused.size();
     std::vector<ChainState> hs(nf);
-    std::vector<int64_t> base(nf + 1, 0);
+    std::vector<int64_t> base(nf + 1, 0);        // first block of every network
     for (int i = 0; i < nf; ++i) {
         hs[i] = fused[i]->S;
-        base[i + 1] = base[i] + fused[i]->S.C;
+        base[i + 1] = base[i] + (fused[i]->S.C + BATCH_WARPS - 1) / BATCH_WARPS;
     }
     uint8_t* d = (uint8_t*)b->dev;
     ChainState* d_states = (ChainState*)d;
-    FusedArgs* d_fargs = (FusedArgs*)(d + sizeof(ChainState) * (nf + 1));
-    int64_t* d_base = (int64_t*)((uint8_t*)d_fargs + sizeof(FusedArgs) * (nf + 1));
-    int* d_iters = (int*)(d_base + nf + 1);
+    int64_t* d_base = (int64_t*)(d + sizeof(ChainState) * (nf + 1));
     BN_CUDA(cudaMemcpyAsync(d_states, hs.data(), sizeof(ChainState) * nf, cudaMemcpyHostToDevice, s));
     BN_CUDA(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, s));
-    std::vector<FusedArgs> hf(nf);
-    std::vector<int> hit(nf);
-    const unsigned blocks = (unsigned)((base[nf] + FUSED_WARPS - 1) / FUSED_WARPS);
+    const unsigned blocks = (unsigned)base[nf];
     int cap = 0;
     for (bn_chains* c : fused)
         if (c->t->alive_total <= SURV_CAP_MAX) cap = std::max(cap, (int)c->t->alive_total);
@@ -1358,30 +1385,47 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
         int rc = fused_smem_setup(cap, &smem);
         if (rc) return rc;
     }
-    for (int64_t done = 0; done < steps;) {
+    // every launch's arguments up front (one upload, no synchronisation between launches)
+    const int64_t nl = (steps + FUSED_ITERS - 1) / FUSED_ITERS;
+    std::vector<FusedArgs> hf((size_t)nl * nf);
+    std::vector<int> hit((size_t)nl * nf);
+    for (int64_t l = 0; l < nl; ++l) {
+        const int64_t done = l * FUSED_ITERS;
         const int it = (int)std::min<int64_t>(FUSED_ITERS, steps - done);
         for (int i = 0; i < nf; ++i) {
             const bn_table* t = fused[i]->t;
-            hf[i].amask = t->amask;
-            hf[i].aspos = t->aspos;
-            hf[i].aoff = t->aoff;
-            hf[i].acnt = t->acnt;
-            hf[i].t0 = fused[i]->steps + done;
-            hf[i].iters = it;
-            hf[i].staged = t->alive_total <= cap ? 1 : 0;
-            hf[i].cap = cap;
-            hf[i].margin_x = mh_margin(t->n, t->max_abs_survivor);
-            hit[i] = it;
+            FusedArgs& f = hf[(size_t)l * nf + i];
+            f.amask = t->amask;
+            f.aspos = t->aspos;
+            f.aoff = t->aoff;
+            f.acnt = t->acnt;
+            f.t0 = fused[i]->steps + done;
+            f.iters = it;
+            f.staged = t->alive_total <= cap ? 1 : 0;
+            f.cap = cap;
+            f.margin_x = mh_margin(t->n, t->max_abs_survivor);
+            hit[(size_t)l * nf + i] = it;
         }
-        BN_CUDA(cudaMemcpyAsync(d_fargs, hf.data(), sizeof(FusedArgs) * nf, cudaMemcpyHostToDevice, s));
-        BN_CUDA(cudaMemcpyAsync(d_iters, hit.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s));
-        k_batch_fused<<<blocks, 32 * FUSED_WARPS, smem, s>>>(d_states, d_fargs, d_base, nf);
-        BN_LAUNCH_CHECK("k_batch_fused");
-        k_batch_advance<<<(nf + 127) / 128, 128, 0, s>>>(d_states, d_iters, nf);
-        BN_LAUNCH_CHECK("k_batch_advance");
-        BN_CUDA(cudaStreamSynchronize(s));     // the host argument arrays are reused
-        done += it;
     }
+    uint8_t* args = nullptr;
+    const size_t fbytes = sizeof(FusedArgs) * hf.size(), ibytes = sizeof(int) * hit.size();
+    BN_CUDA(cudaMallocAsync((void**)&args, fbytes + ibytes + 16, s));
+    struct Free {
+        uint8_t* p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{args, s};
+    FusedArgs* d_fargs = (FusedArgs*)args;
+    int* d_iters = (int*)(args + fbytes);
+    BN_CUDA(cudaMemcpyAsync(d_fargs, hf.data(), fbytes, cudaMemcpyHostToDevice, s));
+    BN_CUDA(cudaMemcpyAsync(d_iters, hit.data(), ibytes, cudaMemcpyHostToDevice, s));
+    for (int64_t l = 0; l < nl; ++l) {
+        k_batch_fused<<<blocks, 32 * BATCH_WARPS, smem, s>>>(d_states, d_fargs + (size_t)l * nf, d_base, nf);
+        BN_LAUNCH_CHECK("k_batch_fused");
+        k_batch_advance<<<(nf + 127) / 128, 128, 0, s>>>(d_states, d_iters + (size_t)l * nf, nf);
+        BN_LAUNCH_CHECK("k_batch_advance");
+    }
+    BN_CUDA(cudaStreamSynchronize(s));     // the host argument arrays are released after this
     for (bn_chains* c : fused) c->steps += steps;
     return BN_OK;
 }

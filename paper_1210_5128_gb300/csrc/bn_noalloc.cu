@@ -104,7 +104,9 @@ extern "C" int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders,
     // counts, masks and per-item results are rewritten by k_pred_lists before use
     BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
     if ((rc = launch_pred_lists(orders, B, n, d_pc, d_best, d_cnt, d_status, s))) return rc;
-    if ((rc = launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_status, s))) return rc;
+    rc = scan_nodes_fits(t, B) ? launch_scan_nodes(t, B, d_pc, d_best, d_status, s)
+                               : launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_status, s);
+    if (rc) return rc;
     k_noalloc_reduce<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, best_rank, order_score);
     BN_LAUNCH_CHECK("k_noalloc_reduce");
     uint32_t st = 0;

@@ -13,7 +13,9 @@
 // against its item's predecessor mask and keeps a running min of spos.  So the table is
 // read once per 256 orders instead of once per order, and a test is a 64-bit AND-NOT,
 // a zero test and one unsigned min.  When a block holds fewer than 256 items, its spare
-// warps take a share of the entries of the same items.  Chunks combine with atomicMin.
+// warps take a share of the entries of the same items, and below 32 items the lanes of a
+// warp split each item's entries as well (so a batch of a few orders streams the table at
+// memory speed instead of one active lane per warp).  Chunks combine with atomicMin.
 #include <algorithm>
 #include <cstring>
 
@@ -49,7 +51,8 @@ static ScanPlan plan_for(const bn_table* t, int groups, int64_t target, int sub)
     ScanPlan p;
     p.sub = sub;
     const int64_t units = t->Sp / SUBQ;
-    int64_t nchunk = (target + (int64_t)t->n * groups - 1) / ((int64_t)t->n * groups);
+    // whole waves: at most `target` blocks
+    int64_t nchunk = target / ((int64_t)t->n * groups);
     nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, units));
     const int64_t chunk = round_up((t->Sp + nchunk - 1) / nchunk, SUBQ);
     p.chunk = chunk;
@@ -67,7 +70,10 @@ ScanPlan plan_scan(const bn_table* t, int max_items)
         p.chunk = t->tuned_chunk[groups];
         return p;
     }
-    return plan_for(t, groups, (int64_t)sm_count() * 4 * 2, 1024);   // two waves of four blocks per SM
+    // four blocks per SM: one wave for a few items per node (the scan streams the table at
+    // memory speed, and a second, partial wave would idle most SMs), else two
+    const int waves = max_items <= 32 ? 1 : 2;
+    return plan_for(t, groups, (int64_t)sm_count() * 4 * waves, 1024);
 }
 
 template <int SCAN_SUB>
@@ -98,13 +104,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     const int64_t e1 = min(e0 + A.chunk, A.Sp);
     if (e0 >= e1) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // G warps' worth of items; the spare warps split the entries of the same items
+    // G warps' worth of items; the spare warps split the entries of the same items.  With
+    // fewer than 32 items a warp holds all of them, LPI lanes per item, and the LPI lanes
+    // of an item split its entries too.
     const int here = min(SCAN_THREADS, cnt - g0);
-    const int G = (here + 31) >> 5;
+    const int ipw = here >= 32 ? 32 : (here <= 1 ? 1 : 1 << (32 - __clz(here - 1)));   // items per warp
+    const int LPI = 32 / ipw;                                                          // lanes per item
+    const int G = (here + ipw - 1) / ipw;
     const int split = SCAN_WARPS / G;
     const int ig = warp % G, sp = warp / G;
     const bool warp_on = sp < split;
-    const int item = g0 + ig * 32 + lane;
+    const int item = g0 + ig * ipw + lane / LPI;
+    const int sub = lane % LPI;
     const bool active = warp_on && item < cnt;
     const uint64_t npc = active ? ~A.list_pc[(size_t)node * A.cap + item] : ~0ull;
     const int nsub = (int)((e1 - e0 + SCAN_SUB - 1) / SCAN_SUB);
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
             const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
             const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
 #pragma unroll 4
-            for (int j = sp; j < pairs; j += split) {
+            for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
                 const uint2 pp = P[j];
                 const ulonglong2 mm = M[j];
                 if ((mm.x & npc) == 0ull) b0 = min(b0, pp.x);
@@ -159,8 +170,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
         }
         return;
     }
-    const uint32_t b = min(b0, b1);
-    if (active && b != SPOS_NONE) atomicMin(&A.list_best[(size_t)node * A.cap + item], b);
+    uint32_t b = min(b0, b1);
+    for (int off = 1; off < LPI; off <<= 1) b = min(b, __shfl_xor_sync(0xffffffffu, b, off));
+    if (active && sub == 0 && b != SPOS_NONE) atomicMin(&A.list_best[(size_t)node * A.cap + item], b);
 }
 
 int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_count, const uint64_t* list_pc,
@@ -192,6 +204,136 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
     else if (v == 1) k_scan<1024><<<grid, SCAN_THREADS, ScanCfg<1024>::SMEM, s>>>(A);
     else k_scan<512><<<grid, SCAN_THREADS, ScanCfg<512>::SMEM, s>>>(A);
     BN_LAUNCH_CHECK("k_scan");
+    return BN_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// A few orders for every node (n x B <= 256 items, bn_score_orders): a block owns a slice
+// of the rank range for all nodes and orders, so the shared candidate-mask table is read
+// once per slice instead of once per node, and the slice's sorted positions of all nodes
+// come from the entry-major copy spos_t as one contiguous bulk copy per stage.  Thread
+// (b, i) tests every entry of the slice for node i of order b; the threads of a warp read
+// consecutive words of a staged row.
+// ---------------------------------------------------------------------------------
+static constexpr int NS_SUB = 128;             // entries per stage
+static constexpr int NS_STAGES = 3;
+
+__host__ __device__ constexpr size_t ns_stage_bytes(int n) { return (size_t)NS_SUB * 8 + (size_t)n * NS_SUB * 4; }
+__host__ __device__ constexpr size_t ns_smem(int n) { return NS_STAGES * ns_stage_bytes(n) + 8 * NS_STAGES; }
+
+struct NodeScanArgs {
+    const uint32_t* spos_t;        // [Sp][n]
+    const uint64_t* pst;
+    int64_t Sp;
+    int n, B;
+    int64_t chunk;                 // entries per block (multiple of NS_SUB)
+    const uint64_t* list_pc;       // [n][B]
+    uint32_t* list_best;           // [n][B]
+    uint32_t* status;
+};
+
+// T consecutive threads per (order, node) pair; thread `sub` tests the entry pairs
+// (2j, 2j + 1), j = sub mod T, of every staged slice
+template <int T>
+__global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const size_t SB = ns_stage_bytes(A.n);
+    uint64_t* bar = (uint64_t*)(smem + NS_STAGES * SB);
+    const int64_t e0 = (int64_t)blockIdx.x * A.chunk;
+    const int64_t e1 = min(e0 + A.chunk, A.Sp);
+    if (e0 >= e1) return;                                           // block-uniform
+    const int nsub = (int)((e1 - e0) / NS_SUB);
+    const int tid = threadIdx.x;
+    const int pairs = A.n * A.B;
+    const bool active = tid < pairs * T;
+    const int pr = tid / T, sub = tid - pr * T;
+    const int b = active ? pr / A.n : 0, i = active ? pr - b * A.n : 0;
+    const uint64_t npc = active ? ~A.list_pc[(size_t)i * A.B + b] : ~0ull;
+    const uint32_t rows = (uint32_t)(A.n * NS_SUB * 4);
+    uint64_t pol_stream = 0, pol_keep = 0;
+    if (tid == 0) {
+        pol_stream = l2_policy_evict_first();
+        pol_keep = l2_policy_evict_last();
+        for (int st = 0; st < NS_STAGES; ++st) mbar_init(&bar[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // thread 0 stages slice `it` in buffer `st`: the masks, then all nodes' positions
+    auto issue = [&](int it, int st) {
+        uint8_t* base = smem + (size_t)st * SB;
+        const int64_t e = e0 + (int64_t)it * NS_SUB;
+        mbar_arrive_expect_tx(&bar[st], (uint32_t)(NS_SUB * 8) + rows);
+        bulk_g2s(base, A.pst + e, NS_SUB * 8, &bar[st], pol_keep);
+        bulk_g2s(base + NS_SUB * 8, A.spos_t + (size_t)e * A.n, rows, &bar[st], pol_stream);
+    };
+    if (tid == 0)
+        for (int st = 0; st < NS_STAGES && st < nsub; ++st) issue(st, st);
+    uint32_t best0 = SPOS_NONE, best1 = SPOS_NONE;
+    const int n = A.n;
+    int it = 0;
+    bool timed_out = false;
+    for (; it < nsub; ++it) {
+        const int st = it % NS_STAGES;
+        const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS_STAGES) & 1), WAIT_TIMEOUT_NS);
+        if (ok && active) {
+            const ulonglong2* M2 = (const ulonglong2*)(smem + (size_t)st * SB);
+            const uint32_t* P = (const uint32_t*)(smem + (size_t)st * SB + NS_SUB * 8) + i;
+#pragma unroll
+            for (int q = 0; q < NS_SUB / 2 / T; ++q) {
+                const int j = q * T + sub;
+                const ulonglong2 mm = M2[j];
+                const uint32_t p0 = P[(2 * j) * n], p1 = P[(2 * j + 1) * n];
+                if ((mm.x & npc) == 0ull) best0 = min(best0, p0);
+                if ((mm.y & npc) == 0ull) best1 = min(best1, p1);
+            }
+        }
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        if (tid == 0 && it + NS_STAGES < nsub) issue(it + NS_STAGES, st);
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            atomicOr(A.status, STATUS_TIMEOUT);
+            for (int j = it; j < nsub && j < it + NS_STAGES; ++j)
+                mbar_wait_bounded(&bar[j % NS_STAGES], (uint32_t)((j / NS_STAGES) & 1), WAIT_TIMEOUT_NS);
+        }
+        return;
+    }
+    uint32_t best = min(best0, best1);
+#pragma unroll
+    for (int off = 1; off < T; off <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if (active && sub == 0 && best != SPOS_NONE) atomicMin(&A.list_best[(size_t)i * A.B + b], best);
+}
+
+bool scan_nodes_fits(const bn_table* t, int B) { return t->scan_mode == BN_SCAN_FULL && B >= 1 && t->n * B <= 256; }
+
+int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_t* list_best, uint32_t* status,
+                      cudaStream_t s)
+{
+    const size_t smem = ns_smem(t->n);
+    static bool attr[64] = {false};
+    const int d = device_id();
+    if (d < 64 && !attr[d]) {
+        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
+        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
+        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
+        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
+        attr[d] = true;
+    }
+    // threads per (order, node) pair: as many as the block holds, at most eight
+    int T = 1;
+    while (T < 8 && 2 * T * t->n * B <= 256) T *= 2;
+    // whole waves: as many blocks per SM as shared memory holds (at most four)
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(220 * 1024) / smem));
+    const int64_t want = (int64_t)sm_count() * per_sm;
+    const int64_t chunk = round_up((t->Sp + want - 1) / want, NS_SUB);
+    NodeScanArgs A{t->spos_t, t->pst, t->Sp, t->n, B, chunk, list_pc, list_best, status};
+    const unsigned grid = (unsigned)((t->Sp + chunk - 1) / chunk);
+    if (T == 8) k_scan_nodes<8><<<grid, 256, smem, s>>>(A);
+    else if (T == 4) k_scan_nodes<4><<<grid, 256, smem, s>>>(A);
+    else if (T == 2) k_scan_nodes<2><<<grid, 256, smem, s>>>(A);
+    else k_scan_nodes<1><<<grid, 256, smem, s>>>(A);
+    BN_LAUNCH_CHECK("k_scan_nodes");
     return BN_OK;
 }
 
@@ -348,7 +490,9 @@ static int score_orders_impl(const bn_table* t, const uint8_t* orders, int B, ui
     int rc = launch_pred_lists(d_orders, B, n, d_pc, d_best, d_cnt, d_st, s);
     if (rc) return rc;
     if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
-    if ((rc = launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_st, s))) return rc;
+    rc = scan_nodes_fits(t, B) ? launch_scan_nodes(t, B, d_pc, d_best, d_st, s)
+                               : launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_st, s);
+    if (rc) return rc;
     if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, d_rank, d_score);
     BN_LAUNCH_CHECK("k_reduce_orders");

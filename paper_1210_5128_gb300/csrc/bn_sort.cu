@@ -160,6 +160,24 @@ __global__ void k_rs_finish(const uint32_t* __restrict__ vals, int64_t N, int64_
     spos[(node0 + i) * Sp + r] = (uint32_t)p;
 }
 
+// spos_t[r][i] = spos[i][r]: 32 x 32 tiles through shared memory (coalesced both ways)
+__global__ void k_spos_transpose(const uint32_t* __restrict__ spos, int n, int64_t Sp, uint32_t* __restrict__ spos_t)
+{
+    __shared__ uint32_t tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int i0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;          // 32 x 8 threads
+    for (int y = ty; y < 32; y += 8) {
+        const int i = i0 + y;
+        if (i < n) tile[y][tx] = spos[(size_t)i * Sp + r0 + tx];
+    }
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int i = i0 + tx;
+        if (i < n) spos_t[(size_t)(r0 + y) * n + i] = tile[tx][y];
+    }
+}
+
 __global__ void k_spos_pad(uint32_t* __restrict__ spos, uint32_t* __restrict__ srank, int n, int64_t S, int64_t Sp)
 {
     const int64_t pad = Sp - S;
@@ -240,6 +258,9 @@ int rank_entries(bn_table* t, cudaStream_t s)
         k_spos_pad<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(t->spos, t->srank, t->n, S, t->Sp);
         BN_LAUNCH_CHECK("k_spos_pad");
     }
+    k_spos_transpose<<<dim3((unsigned)(t->Sp / 32), (unsigned)((t->n + 31) / 32)), dim3(32, 8), 0, s>>>(t->spos, t->n, t->Sp,
+                                                                                                    t->spos_t);
+    BN_LAUNCH_CHECK("k_spos_transpose");
     return BN_OK;
 }
 

@@ -278,17 +278,19 @@ static int table_alloc(int n, int k, bn_table** out)
     if (e == cudaSuccess) e = cudaMalloc(&t->pst, sizeof(uint64_t) * (size_t)t->Sp);
     if (e == cudaSuccess) e = cudaMalloc(&t->spos, sizeof(uint32_t) * (size_t)n * (size_t)t->Sp);
     if (e == cudaSuccess) e = cudaMalloc(&t->srank, sizeof(uint32_t) * (size_t)n * (size_t)t->Sp);
+    if (e == cudaSuccess) e = cudaMalloc(&t->spos_t, sizeof(uint32_t) * (size_t)n * (size_t)t->Sp);
     if (e != cudaSuccess) {
         cudaFree(t->keys);
         cudaFree(t->pst);
         cudaFree(t->spos);
         cudaFree(t->srank);
+        cudaFree(t->spos_t);
         delete t;
         cudaGetLastError();
         return set_error(BN_ENOMEM, "table allocation of %lld entries failed: %s",
                          (long long)((int64_t)n * num_sets_host(n - 1, k)), cudaGetErrorString(e));
     }
-    t->bytes = (sizeof(int64_t) + 2 * sizeof(uint32_t)) * (size_t)n * (size_t)t->Sp + sizeof(uint64_t) * (size_t)t->Sp;
+    t->bytes = (sizeof(int64_t) + 3 * sizeof(uint32_t)) * (size_t)n * (size_t)t->Sp + sizeof(uint64_t) * (size_t)t->Sp;
     *out = t;
     return BN_OK;
 }
@@ -642,6 +644,7 @@ extern "C" void bn_table_free(bn_table* t)
     cudaFree(t->pst);
     cudaFree(t->spos);
     cudaFree(t->srank);
+    cudaFree(t->spos_t);
     cudaFree(t->alive_block);
     delete t;
 }

@@ -13,6 +13,7 @@ struct bn_table {
     uint32_t* spos = nullptr;  // [n][Sp] position of the entry when the node's entries are
                                // ordered by score descending, rank ascending (padding: ~0)
     uint32_t* srank = nullptr; // [n][Sp] inverse of spos: rank at sorted position p
+    uint32_t* spos_t = nullptr;// [Sp][n] spos entry-major (scans of a few orders for every node)
     size_t bytes = 0;
     int scan_mode = 0;         // BN_SCAN_FULL or BN_SCAN_PRUNED
     // entries not dominated by a proper subset, per node in sorted-position order
@@ -60,6 +61,12 @@ constexpr uint32_t SPOS_NONE = 0xffffffffu;
 int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_count,
                 const uint64_t* list_pc, uint32_t* list_best, int cap, uint32_t* status,
                 cudaStream_t s);
+
+// The same for B orders of every node when n * B <= 256 and the table is scanned in full
+// (scan_nodes_fits): one pass over the rank range for all nodes (list layout [n][B]).
+bool scan_nodes_fits(const bn_table* t, int B);
+int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_t* list_best, uint32_t* status,
+                      cudaStream_t s);
 
 // Candidate-space predecessor masks of B orders written as node-major work lists:
 // list_pc[i * B + b] (item b of node i is order b), list_best[i * B + b] = SPOS_NONE,

@@ -20,17 +20,32 @@ def _check_shared(gpu, tab, k, orders):
     return br, sc
 
 
-@pytest.mark.parametrize("B", [1, 2, 37, 256, 300])
+@pytest.mark.parametrize("B", [1, 2, 3, 5, 8, 17, 31, 33, 37, 256, 300])
 def test_shared_table_n6(gpu, B):
     data, arity, k, R, _ = synth.workload("n6_k2_m100")
     tab = oracle.build_table(data, arity, k, R=R)
     _check_shared(gpu, tab, k, synth.random_orders(6, B, B))
 
 
-def test_shared_table_n20_prior(gpu):
+@pytest.mark.parametrize("B", [1, 3, 9, 16, 97])
+def test_shared_table_n20_prior(gpu, B):
+    """Batches below 32 orders split each order's entries over the lanes of a warp."""
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     tab = oracle.build_table(data, arity, k, R=R)
-    _check_shared(gpu, tab, k, synth.random_orders(20, 97, 4))
+    _check_shared(gpu, tab, k, synth.random_orders(20, B, 4 + B))
+
+
+def test_profiled_scoring_equals_plain(gpu):
+    import torch
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    for B in (1, 7, 300):
+        orders = synth.random_orders(20, B, 40 + B)
+        br, sc = gpu.score_orders(t, orders)
+        br2, sc2, ms = gpu.score_orders_profiled(t, torch.as_tensor(orders, device="cuda"))
+        assert np.array_equal(br, br2.cpu().numpy().astype(np.uint32))
+        assert np.array_equal(sc, sc2.cpu().numpy())
+        assert ms > 0.0
 
 
 def test_all_720_orders_n6(gpu):
@@ -51,6 +66,7 @@ def test_ties_lowest_rank(gpu):
     rng = np.random.default_rng(0)
     tab = rng.integers(-3, 1, size=(n, S)).astype(np.float64)   # many exact ties
     _check_shared(gpu, tab, k, synth.random_orders(n, 300, 2))
+    _check_shared(gpu, tab, k, synth.random_orders(n, 5, 3))
 
 
 def test_identity_and_reverse_orders(gpu):
@@ -116,7 +132,7 @@ def test_autotuned_tiling_gives_identical_results(gpu):
     assert np.array_equal(br0, br1) and np.array_equal(sc0, sc1)
 
 
-@pytest.mark.parametrize("name,B", [("n40_k4_m2000", 512), ("n60_k4_m1000", 256)])
+@pytest.mark.parametrize("name,B", [("n40_k4_m2000", 512), ("n60_k4_m1000", 256), ("n60_k4_m1000", 4)])
 def test_full_size_sampled_orders(gpu, name, B):
     """The full-size table built on the GPU, scored in the bench's batch shape; a seeded
     sample of the orders is re-scored by the oracle on the downloaded table."""
