@@ -82,21 +82,56 @@ __device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, 
     }
 }
 
-// first survivor from j on (score order) whose parent set lies inside the predecessors
-// (npc = their complement): four independent loads per round; the node's last survivor,
-// the empty set, always qualifies, so no load passes j1 - 1
-__device__ __forceinline__ uint32_t first_consistent(const uint64_t* m, uint32_t j, uint32_t j1, uint64_t npc)
+// The span's re-scoring walks, lane by lane: every lane has up to two nodes (h = 0, 1;
+// act[h]) and finds for each the first survivor j in [j[h], j1[h]) with (m[j] & npc[h]) == 0
+// (the last survivor, the empty set, always qualifies).  A lane walks its own nodes for
+// 16 survivors; nodes still open then are walked by the whole warp, 32 survivors a round.
+// On return j[h] holds the answer.  All 32 lanes must call it.
+__device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], const uint32_t (&j1)[2],
+                                          const uint64_t (&npc)[2], const bool (&act)[2], int lane)
 {
-    while (j + 4 <= j1) {
-        const uint64_t a0 = m[j], a1 = m[j + 1], a2 = m[j + 2], a3 = m[j + 3];
-        if ((a0 & npc) == 0ull) return j;
-        if ((a1 & npc) == 0ull) return j + 1;
-        if ((a2 & npc) == 0ull) return j + 2;
-        if ((a3 & npc) == 0ull) return j + 3;
-        j += 4;
+    bool open[2] = {false, false};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!act[h]) continue;
+        uint32_t x = j[h];
+        bool found = false;
+        for (int r = 0; r < 4 && !found; ++r) {
+            if (x + 4 <= j1[h]) {
+                const uint64_t a0 = m[x], a1 = m[x + 1], a2 = m[x + 2], a3 = m[x + 3];
+                if ((a0 & npc[h]) == 0ull) found = true;
+                else if ((a1 & npc[h]) == 0ull) { x += 1; found = true; }
+                else if ((a2 & npc[h]) == 0ull) { x += 2; found = true; }
+                else if ((a3 & npc[h]) == 0ull) { x += 3; found = true; }
+                else x += 4;
+            } else {
+                while (x + 1 < j1[h] && (m[x] & npc[h]) != 0ull) ++x;
+                found = true;
+            }
+        }
+        j[h] = x;
+        open[h] = !found;
     }
-    while (j + 1 < j1 && (m[j] & npc) != 0ull) ++j;
-    return j;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned pend = __ballot_sync(0xffffffffu, open[h]);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const uint32_t js = __shfl_sync(0xffffffffu, j[h], src), je = __shfl_sync(0xffffffffu, j1[h], src);
+            const uint64_t np = __shfl_sync(0xffffffffu, npc[h], src);
+            uint32_t hit = je - 1;
+            for (uint32_t base = js; base < je; base += 32) {
+                const uint32_t idx = base + lane;
+                const unsigned b = __ballot_sync(0xffffffffu, idx < je && (m[idx] & np) == 0ull);
+                if (b) {
+                    hit = base + __ffs(b) - 1;
+                    break;
+                }
+            }
+            if (lane == src) j[h] = hit;
+        }
+    }
 }
 
 // rounding bound of the MH test's right-hand side: two sequential sums of n entries of

@@ -703,23 +703,35 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
                 srk = (const uint32_t*)(sreg + L.so_rk);
                 soff = (const uint32_t*)(sreg + L.so_off);
             }
-            double dpart = 0.0;
+            // survivors in score order: the first consistent one wins (the empty set, always
+            // consistent, is the last survivor)
+            uint32_t wj[2] = {0, 0}, wj1[2] = {0, 0};
+            uint64_t wnpc[2] = {0, 0};
+            bool act[2] = {false, false};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int p = lane + 32 * h;
                 if (p < n && p >= a && p <= b) {
                     const int nd = v[h];
                     const uint64_t excl = (h == 0 ? s0 : (s1 | first_half)) & ~bit[h];
-                    const uint64_t npc = ~compress_pred(excl, nd);
-                    // survivors in score order: the first consistent one wins (the empty
-                    // set, always consistent, is the last survivor)
-                    const uint32_t j = first_consistent(smask, soff[nd], soff[nd + 1], npc);
-                    const uint32_t r = srk[j];
-                    const int64_t k = skey[j];
-                    L.prank[(size_t)c * n + p] = r;
-                    L.pkey[(size_t)c * n + p] = k;
-                    dpart += key_to_double(k) - key_to_double(W.key[nd]);
+                    wnpc[h] = ~compress_pred(excl, nd);
+                    wj[h] = soff[nd];
+                    wj1[h] = soff[nd + 1];
+                    act[h] = true;
                 }
+            }
+            span_walk(smask, wj, wj1, wnpc, act, lane);
+            double dpart = 0.0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!act[h]) continue;
+                const int p = lane + 32 * h;
+                const int nd = v[h];
+                const uint32_t r = srk[wj[h]];
+                const int64_t k = skey[wj[h]];
+                L.prank[(size_t)c * n + p] = r;
+                L.pkey[(size_t)c * n + p] = k;
+                dpart += key_to_double(k) - key_to_double(W.key[nd]);
             }
 #pragma unroll
             for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);

@@ -384,32 +384,37 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         // current prefix with node va replaced by vb between a and b)
         int node[2] = {-1, -1};
         uint32_t nrank[2] = {0, 0};
-        bool moved = false;
+        uint32_t wj[2] = {0, 0}, wj1[2] = {0, 0};
+        uint64_t wnpc[2] = {0, 0};
+        bool act[2] = {false, false};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int p = lane + 32 * h;
             if (p < n && p >= a && p <= b) {
                 const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
                 const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
-                const uint64_t npc = ~compress_pred(excl, nd);
-                if (F.staged) {
-                    // survivors of the node in score order: the first consistent one wins
-                    const uint32_t j = first_consistent(c_mask, c_off[nd], c_off[nd + 1], npc);
-                    nrank[h] = c_rank[j];
-                    W.nkey[nd] = c_key[j];
-                } else {
-                    const uint64_t* M = F.amask + F.aoff[nd];
-                    const uint32_t cnt = F.acnt[nd];
-                    uint32_t sp = 0;
-                    for (uint32_t j = 0; j < cnt; ++j) {
-                        if ((M[j] & npc) == 0ull) { sp = F.aspos[F.aoff[nd] + j]; break; }
-                    }
-                    nrank[h] = S.srank[(size_t)nd * S.Sp + sp];
-                    W.nkey[nd] = S.keys[(size_t)nd * S.Sp + nrank[h]];
-                }
+                wnpc[h] = ~compress_pred(excl, nd);
+                wj[h] = F.staged ? c_off[nd] : F.aoff[nd];
+                wj1[h] = F.staged ? c_off[nd + 1] : F.aoff[nd] + F.acnt[nd];
                 node[h] = nd;
-                moved |= nrank[h] != W.rank[nd];
+                act[h] = true;
             }
+        }
+        // survivors of each node in score order: the first consistent one wins
+        span_walk(F.staged ? c_mask : F.amask, wj, wj1, wnpc, act, lane);
+        bool moved = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!act[h]) continue;
+            const int nd = node[h];
+            if (F.staged) {
+                nrank[h] = c_rank[wj[h]];
+                W.nkey[nd] = c_key[wj[h]];
+            } else {
+                nrank[h] = S.srank[(size_t)nd * S.Sp + F.aspos[wj[h]]];
+                W.nkey[nd] = S.keys[(size_t)nd * S.Sp + nrank[h]];
+            }
+            moved |= nrank[h] != W.rank[nd];
         }
         moved = __any_sync(0xffffffffu, moved);
         items += b - a + 1;
