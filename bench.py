@@ -361,6 +361,27 @@ def main():
                         "calls": len(times), "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
                         "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak})
 
+    # ---- the sum-based order score of the prior scorer (Sec. III.B) on the same table:
+    #      one order, whole-call device time, L2 flushed before every call ------------------
+    o1 = torch.from_numpy(synth.random_orders(n, 1, 101)).to(dev)
+    bn.score_orders_sum(table, o1)
+    sum_times = []
+    for _ in range(5):
+        _flush_l2(torch, flush, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bn.score_orders_sum(table, o1)
+        e1.record()
+        torch.cuda.synchronize()
+        sum_times.append(1000.0 * e0.elapsed_time(e1))
+    sum_score = {"orders": 1, "call_us": float(np.median(sum_times)),
+                 "max_score_scan_us": hbm_leg[0]["scan_us"],
+                 "note": "bn_score_orders_sum: FP64 log10-sum-exp10 over the consistent parent sets of "
+                         "every node (one exp10 per consistent set), against the max-based scan of the "
+                         "same order (roofline_hbm)"}
+
     with torch.cuda.stream(stream):
         # ---- full-table scan sampler ----------------------------------------------------
         full = bn.chains_create(table, args.chains, seed=seed)
@@ -373,6 +394,15 @@ def main():
         scan_ms_full, scan_l_full = bn.chains_step_profiled(full, prof_steps, stream=stream.cuda_stream)
         items_prof = int(bn.chains_read(full, "items")[0]) - i1
         full.free()
+
+        # ---- the same full scan with every parent set unranked on the fly (no table) --------
+        bn.table_set_scan(table, bn.SCAN_UNRANK)
+        unr = bn.chains_create(table, args.chains, seed=seed)
+        bn.chains_step(unr, args.warmup, stream=stream.cuda_stream)
+        unr_steps = max(3, min(args.steps, 50))
+        ms_unr = _timed(bn, torch, unr, unr_steps, stream, pieces=unr_steps, flush=flush)
+        unr.free()
+        bn.table_set_scan(table, bn.SCAN_FULL)
 
         # ---- pruned scan sampler (headline) ----------------------------------------------
         torch.cuda.synchronize()
@@ -525,8 +555,13 @@ def main():
                             "survivors_per_node_max": int(survivors.max()),
                             "survivor_fraction": float(survivors.sum() / (n * S)), "prune_s": prune_s},
             "full_scan": {"value": world * args.chains * args.steps / (ms_full / 1000.0),
-                          "ms_per_step": ms_full / args.steps, "items_per_step": items_full / args.steps},
+                          "ms_per_step": ms_full / args.steps, "items_per_step": items_full / args.steps,
+                          "unranked_sets": {"value": world * args.chains * unr_steps / (ms_unr / 1000.0),
+                                            "ms_per_step": ms_unr / unr_steps, "steps": unr_steps,
+                                            "note": "BN_SCAN_UNRANK: every parent set computed from its rank "
+                                                    "in the scan instead of read from the parent-set table"}},
             "ess": ess,
+            "sum_score": sum_score,
             "uneven_batch": batch,
             "accuracy": accuracy,
             "cpu_baseline": cpu,

@@ -117,6 +117,19 @@ int bn_score_orders(const bn_table* t, const uint8_t* orders, int B, uint32_t* b
 int bn_score_orders_profiled(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
                              double* order_score, int mem, void* stream, double* scan_ms);
 
+/* The sum-based order score of the prior scorer the paper compares its own against
+ * (Sec. III.B): for each order, the log10 of the sum over all graphs consistent with it
+ * of 10^(graph score) = sum_i log10 sum_{parent sets of node i drawn from its
+ * predecessors} 10^entry(i, pi), in FP64.  Per (order, node) the consistent entries are
+ * accumulated as a running (max, shifted sum); partial sums merge in a fixed order (the
+ * result is deterministic for a table and a batch, not bit-equal to a sequential sum).
+ *   orders      B x n uint8 permutations (position -> node)
+ *   order_score B float64 out (may be NULL)
+ *   node_score  B x n float64 out, [b][i] = node i's term (may be NULL)
+ * Scratch is allocated per call.  Errors: BN_EINVAL, BN_ENOMEM, BN_ECUDA. */
+int bn_score_orders_sum(const bn_table* t, const uint8_t* orders, int B, double* order_score,
+                        double* node_score, int mem, void* stream);
+
 /* bn_score_orders without any allocation.  The paper has no counterpart to this call.
  * It is for callers that cannot allocate device memory when they score orders: a host
  * framework whose memory pool owns the device and forbids outside allocations, a
@@ -148,9 +161,14 @@ int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
  *                   a score at least as high and a lower rank.  Results are identical.
  *                   The surviving entries are kept in score order, so each order stops
  *                   at its first consistent one.  The first switch builds them (k <= 7).
+ *   BN_SCAN_UNRANK  every entry, as BN_SCAN_FULL, but each parent set is computed from
+ *                   its rank on the fly (the paper's first strategy, Sec. V.B / Algorithm
+ *                   2, in this library's size-ascending combinatorial number system)
+ *                   instead of read from the parent-set table.  Results are identical. 
  * Errors: BN_EINVAL, BN_ENOMEM, BN_EUNSUPPORTED, BN_ECUDA. */
 #define BN_SCAN_FULL   0
 #define BN_SCAN_PRUNED 1
+#define BN_SCAN_UNRANK 2
 int bn_table_set_scan(bn_table* t, int mode, void* stream);
 /* surviving entries per node after pruning (n int64) */
 int bn_table_pruned(const bn_table* t, int64_t* survivors_per_node);

@@ -82,6 +82,8 @@ def _declare(L):
     L.orc_cand_to_node.argtypes = [C.c_int, C.c_int]
     L.orc_order_score.restype = C.c_double
     L.orc_order_score.argtypes = [_dp, C.c_int, C.c_int, _u8p, _u32p]
+    L.orc_order_score_sum.restype = C.c_double
+    L.orc_order_score_sum.argtypes = [_dp, C.c_int, C.c_int, _u8p, _dp]
     L.orc_greedy_dag.restype = None
     L.orc_greedy_dag.argtypes = [C.c_int, C.c_int, _u32p, _u8p]
     L.orc_graph_score.restype = C.c_double
@@ -192,6 +194,17 @@ def order_score(table, k, order):
     br = np.zeros(n, np.uint32)
     s = lib().orc_order_score(_p(table, _dp), n, k, _p(order, _u8p), _p(br, _u32p))
     return float(s), br
+
+
+def order_score_sum(table, k, order):
+    """The sum-based order score (log10 of the summed 10^score of every consistent
+    graph) and its per-node terms."""
+    table = _c(table, np.float64)
+    n = table.shape[0]
+    order = _c(order, np.uint8)
+    ns = np.zeros(n, np.float64)
+    s = lib().orc_order_score_sum(_p(table, _dp), n, k, _p(order, _u8p), _p(ns, _dp))
+    return float(s), ns
 
 
 def greedy_dag(n, k, best_rank):

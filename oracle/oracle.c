@@ -269,6 +269,45 @@ double orc_order_score(const double* table, int n, int k, const uint8_t* order,
     return total;
 }
 
+double orc_order_score_sum(const double* table, int n, int k, const uint8_t* order, double* node_score)
+{
+    int64_t S = orc_num_sets(n - 1, k);
+    int pos[64];
+    for (int p = 0; p < n; ++p) pos[order[p]] = p;
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int pred[64], np = 0;
+        for (int c = 0; c < n - 1; ++c) {
+            int node = orc_cand_to_node(i, c);
+            if (pos[node] < pos[i]) pred[np++] = c;
+        }
+        int maxj = k < np ? k : np;
+        /* two passes over the same enumeration: the maximum, then the shifted sum */
+        double mx = -INFINITY, sum = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j <= maxj; ++j) {
+                int idx[64], set[64];
+                for (int t = 0; t < j; ++t) idx[t] = t;
+                for (;;) {
+                    for (int t = 0; t < j; ++t) set[t] = pred[idx[t]];
+                    double v = table[(size_t)i * (size_t)S + (size_t)orc_rank(n - 1, k, set, j)];
+                    if (pass == 0) { if (v > mx) mx = v; }
+                    else sum += pow(10.0, v - mx);
+                    int t = j - 1;
+                    while (t >= 0 && idx[t] == np - j + t) --t;
+                    if (t < 0) break;
+                    idx[t] += 1;
+                    for (int u = t + 1; u < j; ++u) idx[u] = idx[u - 1] + 1;
+                }
+            }
+        }
+        double node = mx + log10(sum);
+        if (node_score) node_score[i] = node;
+        total += node;
+    }
+    return total;
+}
+
 void orc_greedy_dag(int n, int k, const uint32_t* best_rank, uint8_t* adj)
 {
     memset(adj, 0, (size_t)n * (size_t)n);

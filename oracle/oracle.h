@@ -6,6 +6,7 @@
  * generator with the CUDA library; it is written directly from the paper:
  *   Eq. (3)-(4)   local score (Bayesian-Dirichlet, log10 space)
  *   Eq. (5)-(6)   graph score and order score (sum over nodes of the best consistent set)
+ *   Sec. III.B    the sum-based order score of the prior scorer the paper compares against
  *   Eq. (7)-(10)  pairwise prior, PPF = 100 (R - 0.5)^3
  *   Algorithm 1   learner loop: score, Metropolis-Hastings test, best graph, swap
  *   Algorithm 2   unranking of the l-th k-combination in lexicographic order
@@ -55,6 +56,13 @@ double orc_order_score(const double* table, int n, int k, const uint8_t* order,
 void   orc_greedy_dag(int n, int k, const uint32_t* best_rank, uint8_t* adj);
 /* Eq. (9) score of a DAG given per-node ranks: sum over nodes ascending */
 double orc_graph_score(const double* table, int n, int k, const uint32_t* ranks);
+/* The sum-based order score of the prior scorer the paper compares against (Sec. III.B):
+ * log10 of the sum over all graphs consistent with the order of 10^score(G), which
+ * factorises over nodes into sum_i log10 sum_{consistent pi} 10^ls(i, pi).  Per node the
+ * consistent sets are enumerated as in orc_order_score, the terms summed in that order
+ * after shifting by the node's maximum; nodes summed in ascending id.  node_score (n,
+ * may be NULL) receives the per-node values. */
+double orc_order_score_sum(const double* table, int n, int k, const uint8_t* order, double* node_score);
 
 /* ---- Philox4x64-10 (Salmon et al., SC'11) --------------------------------------- */
 void   orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);

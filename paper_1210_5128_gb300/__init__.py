@@ -78,6 +78,7 @@ def _load():
     _L.bn_score_orders.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp]
     _L.bn_score_orders_noalloc.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp]
     _L.bn_score_orders_profiled.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp, C.POINTER(C.c_double)]
+    _L.bn_score_orders_sum.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp]
     _L.bn_unrank.argtypes = [C.c_int, C.c_int, C.c_int64, C.POINTER(C.c_uint64)]
     _L.bn_rank.argtypes = [C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_int64)]
     _L.bn_chains_create.argtypes = [_vp, C.POINTER(MCMCParams), _vp, C.c_int, _vp, C.POINTER(_vp)]
@@ -287,7 +288,27 @@ def score_orders_profiled(t: Table, orders):
     return br, sc, ms.value
 
 
-SCAN_FULL, SCAN_PRUNED = 0, 1
+def score_orders_sum(t: Table, orders):
+    """The sum-based order score (bn_score_orders_sum) -> (order score (B,), node terms (B, n));
+    device tensors in, device tensors out; host arrays in, numpy arrays out."""
+    n = table_info(t)["n"]
+    if _is_cuda(orders):
+        import torch
+        o = _dev(orders, torch.uint8)
+        B = o.shape[0]
+        sc = torch.empty((B,), dtype=torch.float64, device=o.device)
+        ns = torch.empty((B, n), dtype=torch.float64, device=o.device)
+        _check(lib().bn_score_orders_sum(t.handle, _ptr(o), B, _ptr(sc), _ptr(ns), MEM_DEVICE, _stream(o)))
+        return sc, ns
+    o = _host(orders, np.uint8).reshape(-1, n)
+    B = o.shape[0]
+    sc = np.empty((B,), np.float64)
+    ns = np.empty((B, n), np.float64)
+    _check(lib().bn_score_orders_sum(t.handle, _ptr(o), B, _ptr(sc), _ptr(ns), MEM_HOST, None))
+    return sc, ns
+
+
+SCAN_FULL, SCAN_PRUNED, SCAN_UNRANK = 0, 1, 2
 
 
 def table_set_scan(t: Table, mode: int):

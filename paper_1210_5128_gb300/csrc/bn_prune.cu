@@ -326,7 +326,8 @@ extern "C" int bn_table_set_scan(bn_table* t, int mode, void* stream)
 {
     set_error(BN_OK, "");
     if (!t) return set_error(BN_EINVAL, "bn_table_set_scan: NULL table");
-    if (mode != BN_SCAN_FULL && mode != BN_SCAN_PRUNED) return set_error(BN_EINVAL, "bn_table_set_scan: mode %d", mode);
+    if (mode != BN_SCAN_FULL && mode != BN_SCAN_PRUNED && mode != BN_SCAN_UNRANK)
+        return set_error(BN_EINVAL, "bn_table_set_scan: mode %d", mode);
     if (mode == BN_SCAN_PRUNED) {
         int rc = prune_table(t, (cudaStream_t)stream);
         if (rc) return rc;

@@ -37,6 +37,8 @@ struct ScanArgs {
     const uint32_t* spos;
     const uint64_t* pst;
     int64_t Sp;
+    int64_t S;             // parent sets per node (entries at or past S are padding)
+    int N, k;              // candidates per node (n - 1) and the size limit
     int nchunk;
     int64_t chunk;
     const uint32_t* list_count;
@@ -76,17 +78,69 @@ ScanPlan plan_scan(const bn_table* t, int max_items)
     return plan_for(t, groups, (int64_t)sm_count() * 4 * waves, 1024);
 }
 
-template <int SCAN_SUB>
+template <int SCAN_SUB, bool UNRANK>
 __device__ __forceinline__ void scan_issue(const ScanArgs& A, int node, int64_t base, int64_t e1, uint32_t* s_sp,
                                            uint64_t* s_msk, uint64_t* bar, uint64_t pol_stream, uint64_t pol_keep)
 {
     const uint32_t cnt = (uint32_t)min((int64_t)SCAN_SUB, e1 - base);
-    mbar_arrive_expect_tx(bar, cnt * 12u);
+    mbar_arrive_expect_tx(bar, cnt * (UNRANK ? 4u : 12u));
     bulk_g2s(s_sp, A.spos + (size_t)node * A.Sp + base, cnt * 4u, bar, pol_stream);
-    bulk_g2s(s_msk, A.pst + base, cnt * 8u, bar, pol_keep);
+    if (!UNRANK) bulk_g2s(s_msk, A.pst + base, cnt * 8u, bar, pol_keep);
 }
 
-template <int SCAN_SUB>
+// ---------------------------------------------------------------------------------
+// Parent sets computed instead of read (the paper's first strategy, Sec. V.B, against
+// the table of its second): the candidate-space mask of rank r in the size-ascending
+// combinatorial number system, and the next rank's from the previous one.
+// bin[c * (k + 1) + t] = C(c, t), c <= 64, t <= k.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t unrank_set(uint64_t r, int N, int k, const uint64_t* bin, int& size)
+{
+    int j = 0;
+    while (j <= k && r >= bin[N * (k + 1) + j]) {
+        r -= bin[N * (k + 1) + j];
+        ++j;
+    }
+    size = j;
+    if (j > k) return ~0ull;                              // padding
+    uint64_t m = 0;
+    int hi = N - 1;
+    for (int t = j; t >= 1; --t) {                        // largest element first
+        int lo = t - 1, h = hi;
+        while (lo < h) {
+            const int mid = (lo + h + 1) >> 1;
+            if (bin[mid * (k + 1) + t] <= r) lo = mid;
+            else h = mid - 1;
+        }
+        m |= 1ull << lo;
+        r -= bin[lo * (k + 1) + t];
+        hi = lo - 1;
+    }
+    return m;
+}
+
+// the set after m in rank order: the next set of the same size in colex order (the next
+// larger mask with as many bits, Gosper's construction), else the first set one larger
+__device__ __forceinline__ uint64_t next_set(uint64_t m, int N, int k, int& size)
+{
+    if (size > k) return ~0ull;
+    uint64_t nm = 0;
+    bool roll = true;
+    if (size > 0) {
+        const uint64_t c = m & (~m + 1ull);
+        const uint64_t r = m + c;
+        nm = (((r ^ m) >> 2) >> (__ffsll((long long)c) - 1)) | r;
+        roll = (r == 0ull) || (N < 64 && (nm >> N) != 0ull);
+    }
+    if (roll) {
+        ++size;
+        if (size > k) return ~0ull;
+        nm = (size >= 64) ? ~0ull : ((1ull << size) - 1ull);
+    }
+    return nm;
+}
+
+template <int SCAN_SUB, bool UNRANK>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
 {
     constexpr int SCAN_STAGES = ScanCfg<SCAN_SUB>::STAGES;
@@ -94,6 +148,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     uint64_t* s_msk = (uint64_t*)smem;                                          // [STAGES][SUB]
     uint32_t* s_sp = (uint32_t*)(smem + sizeof(uint64_t) * SCAN_STAGES * SCAN_SUB);
     uint64_t* bar = (uint64_t*)(smem + (sizeof(uint64_t) + sizeof(uint32_t)) * SCAN_STAGES * SCAN_SUB);
+    uint64_t* s_bin = bar + SCAN_STAGES;                                        // C(c, t) (UNRANK)
 
     const int node = blockIdx.x / A.nchunk;
     const int chunk = blockIdx.x - node * A.nchunk;
@@ -127,10 +182,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
         for (int s = 0; s < SCAN_STAGES; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
+    if (UNRANK)
+        for (int q = threadIdx.x; q < 65 * (A.k + 1); q += SCAN_THREADS)
+            s_bin[q] = c_binom.v[q / (A.k + 1)][q % (A.k + 1)];
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < SCAN_STAGES && s < nsub; ++s)
-            scan_issue<SCAN_SUB>(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_sp + s * SCAN_SUB, s_msk + s * SCAN_SUB, &bar[s],
+            scan_issue<SCAN_SUB, UNRANK>(A, node, e0 + (int64_t)s * SCAN_SUB, e1, s_sp + s * SCAN_SUB, s_msk + s * SCAN_SUB, &bar[s],
                        pol_stream, pol_keep);
     }
 
@@ -140,6 +198,25 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     for (; it < nsub; ++it) {
         const int st = it % SCAN_STAGES;
         const uint32_t parity = (uint32_t)((it / SCAN_STAGES) & 1);
+        if (UNRANK) {
+            // this stage's masks: every thread a run of SUB / 256 consecutive ranks
+            constexpr int PER = SCAN_SUB / SCAN_THREADS;
+            const int64_t base = e0 + (int64_t)it * SCAN_SUB;
+            const int64_t r0 = base + (int64_t)threadIdx.x * PER;
+            uint64_t* dst = s_msk + st * SCAN_SUB + threadIdx.x * PER;
+            if (r0 < e1) {
+                int size = 0;
+                uint64_t m = r0 < A.S ? unrank_set((uint64_t)r0, A.N, A.k, s_bin, size) : ~0ull;
+                if (r0 >= A.S) size = A.k + 1;
+                dst[0] = m;
+#pragma unroll
+                for (int q = 1; q < PER; ++q) {
+                    m = next_set(m, A.N, A.k, size);
+                    dst[q] = m;
+                }
+            }
+            __syncthreads();
+        }
         const bool ok = mbar_wait_bounded(&bar[st], parity, WAIT_TIMEOUT_NS);
         if (ok && warp_on) {
             const int64_t base = e0 + (int64_t)it * SCAN_SUB;
@@ -157,8 +234,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
             const int64_t base = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
-            scan_issue<SCAN_SUB>(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st], pol_stream,
-                       pol_keep);
+            scan_issue<SCAN_SUB, UNRANK>(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st],
+                                         pol_stream, pol_keep);
         }
     }
     if (timed_out) {
@@ -175,6 +252,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     if (active && sub == 0 && b != SPOS_NONE) atomicMin(&A.list_best[(size_t)node * A.cap + item], b);
 }
 
+static constexpr size_t SCAN_BIN_BYTES = 8 * 65 * (MAXK + 1);   // binomial table (UNRANK)
+
+template <int SUB, bool UNRANK>
+static int scan_variant(const ScanArgs& A, dim3 grid, cudaStream_t s)
+{
+    static bool attr_set[64] = {false};
+    const size_t smem = ScanCfg<SUB>::SMEM + (UNRANK ? SCAN_BIN_BYTES : 0);
+    const int d = device_id();
+    if (d < 64 && !attr_set[d]) {
+        BN_CUDA(cudaFuncSetAttribute(k_scan<SUB, UNRANK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[d] = true;
+    }
+    k_scan<SUB, UNRANK><<<grid, SCAN_THREADS, smem, s>>>(A);
+    BN_LAUNCH_CHECK("k_scan");
+    return BN_OK;
+}
+
 int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_count, const uint64_t* list_pc,
                 uint32_t* list_best, int cap, uint32_t* status, cudaStream_t s)
 {
@@ -183,6 +277,9 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
     A.spos = t->spos;
     A.pst = t->pst;
     A.Sp = t->Sp;
+    A.S = t->S;
+    A.N = t->n - 1;
+    A.k = t->k;
     A.nchunk = pl.nchunk;
     A.chunk = pl.chunk;
     A.list_count = list_count;
@@ -190,21 +287,11 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
     A.list_best = list_best;
     A.cap = cap;
     A.status = status;
-    static bool attr_set[64][3] = {{false}};
-    const int d = device_id();
-    const int v = pl.sub >= 2048 ? 2 : (pl.sub >= 1024 ? 1 : 0);
-    if (d < 64 && !attr_set[d][v]) {
-        if (v == 2) BN_CUDA(cudaFuncSetAttribute(k_scan<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<2048>::SMEM));
-        if (v == 1) BN_CUDA(cudaFuncSetAttribute(k_scan<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<1024>::SMEM));
-        if (v == 0) BN_CUDA(cudaFuncSetAttribute(k_scan<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ScanCfg<512>::SMEM));
-        attr_set[d][v] = true;
-    }
     dim3 grid((unsigned)(t->n * pl.nchunk), (unsigned)((cap + SCAN_THREADS - 1) / SCAN_THREADS));
-    if (v == 2) k_scan<2048><<<grid, SCAN_THREADS, ScanCfg<2048>::SMEM, s>>>(A);
-    else if (v == 1) k_scan<1024><<<grid, SCAN_THREADS, ScanCfg<1024>::SMEM, s>>>(A);
-    else k_scan<512><<<grid, SCAN_THREADS, ScanCfg<512>::SMEM, s>>>(A);
-    BN_LAUNCH_CHECK("k_scan");
-    return BN_OK;
+    const bool unrank = t->scan_mode == BN_SCAN_UNRANK;
+    if (pl.sub >= 2048) return unrank ? scan_variant<2048, true>(A, grid, s) : scan_variant<2048, false>(A, grid, s);
+    if (pl.sub >= 1024) return unrank ? scan_variant<1024, true>(A, grid, s) : scan_variant<1024, false>(A, grid, s);
+    return unrank ? scan_variant<512, true>(A, grid, s) : scan_variant<512, false>(A, grid, s);
 }
 
 // ---------------------------------------------------------------------------------

@@ -15,7 +15,7 @@ struct bn_table {
     uint32_t* srank = nullptr; // [n][Sp] inverse of spos: rank at sorted position p
     uint32_t* spos_t = nullptr;// [Sp][n] spos entry-major (scans of a few orders for every node)
     size_t bytes = 0;
-    int scan_mode = 0;         // BN_SCAN_FULL or BN_SCAN_PRUNED
+    int scan_mode = 0;         // BN_SCAN_FULL, BN_SCAN_PRUNED or BN_SCAN_UNRANK
     // entries not dominated by a proper subset, per node in sorted-position order
     // (bn_prune.cu): candidate masks and sorted positions, node offsets and counts
     uint64_t* amask = nullptr;

@@ -140,3 +140,46 @@ def test_ties_go_to_lowest_rank():
     _, br = oracle.order_score(T2, k, o[::-1].copy())
     last = n - 1 - 0
     assert br[0] == 7                      # node 0 is last in the reversed order
+
+
+def _log10_sum_over_consistent_dags(T, n, k, order):
+    """log10 of sum over every graph consistent with the order of 10^(graph score), by
+    enumerating adjacency matrices directly: every subset of the forward pairs (m before
+    i in the order) with in-degree <= k; the graph score adds the table entry of each
+    node's parent set (looked up by the pinned rank helper)."""
+    pos = {int(v): p for p, v in enumerate(order)}
+    fwd = [(m, i) for i in range(n) for m in range(n) if pos[m] < pos[i]]
+    scores = []
+    for bits in range(1 << len(fwd)):
+        parents = [[] for _ in range(n)]
+        for e, (m, i) in enumerate(fwd):
+            if bits >> e & 1:
+                parents[i].append(m)
+        if any(len(p) > k for p in parents):
+            continue
+        s = 0.0
+        for i in range(n):
+            cand = sorted(m if m < i else m - 1 for m in parents[i])
+            s += T[i, oracle.rank(n - 1, k, cand)]
+        scores.append(s)
+    scores = np.array(scores)
+    mx = scores.max()
+    return mx + np.log10(np.power(10.0, scores - mx).sum()), len(scores)
+
+
+@pytest.mark.parametrize("n,k,seed", [(4, 3, 0), (4, 2, 1), (5, 2, 2)])
+def test_sum_score_is_the_sum_over_consistent_graphs(n, k, seed):
+    """Sec. III.B: the prior scorer's order score sums 10^score over every graph
+    consistent with the order; it factorises over nodes, which the oracle computes."""
+    rng = np.random.default_rng(seed)
+    T = rng.normal(scale=1.5, size=(n, oracle.num_sets(n - 1, k)))
+    for order in [np.arange(n, dtype=np.uint8), rng.permutation(n).astype(np.uint8)]:
+        want, ngraphs = _log10_sum_over_consistent_dags(T, n, k, order)
+        got, per_node = oracle.order_score_sum(T, k, order)
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-12)
+        assert ngraphs > n
+        # the first node of the order has only the empty set
+        assert per_node[order[0]] == T[order[0], 0]
+        # max <= sum-based <= max + log10(number of consistent graphs)
+        best = oracle.order_score(T, k, order)[0]
+        assert best <= got + 1e-12 and got <= best + np.log10(ngraphs) + 1e-12
