@@ -275,11 +275,12 @@ struct FusedArgs {
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
 };
 
-// per-warp shared-memory cache of a network's survivors: candidate mask, rank and key of
-// every survivor, and the node offsets
+// shared-memory cache of a network's survivors: candidate mask, key, the OR of the masks of
+// the node's survivors before it, and rank of every survivor (score order), and the node
+// offsets
 __host__ __device__ constexpr size_t surv_cache_bytes(int cap)
 {
-    return (size_t)cap * (8 + 8 + 4) + 4 * (MAXN + 1);
+    return (size_t)cap * (8 + 8 + 8 + 4) + 4 * (MAXN + 1);
 }
 static constexpr int SURV_CAP_MAX = 2400;
 
@@ -293,7 +294,10 @@ struct FusedSmem {
     int64_t nkey[MAXN];
     int64_t since[MAXN];
     uint64_t pre[MAXN];        // nodes at positions < p of the current order
-    uint64_t rx0[32], rx1[32]; // Philox outputs x0, x1 of the next 32 steps
+    uint32_t cj[MAXN];         // cache index of each node's current best survivor
+    uint64_t rx0[32];          // the next 32 steps: Philox x0 (the pair),
+    double ru[32];             //   the MH uniform from x1,
+    double rlo[32], rhi[32];   //   and the fast test's thresholds ln u -/+ its margin
 };
 
 // a network's survivors (mask, rank, key in score order; node offsets) into the block's
@@ -304,8 +308,9 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
     const int n = S.n;
     uint64_t* c_mask = (uint64_t*)cache;
     int64_t* c_key = (int64_t*)(cache + 8 * (size_t)F.cap);
-    uint32_t* c_rank = (uint32_t*)(cache + 16 * (size_t)F.cap);
-    uint32_t* c_off = (uint32_t*)(cache + 20 * (size_t)F.cap);
+    uint64_t* c_orb = (uint64_t*)(cache + 16 * (size_t)F.cap);
+    uint32_t* c_rank = (uint32_t*)(cache + 24 * (size_t)F.cap);
+    uint32_t* c_off = (uint32_t*)(cache + 28 * (size_t)F.cap);
     const uint32_t o0 = F.aoff[0];
     const uint32_t total = F.aoff[n - 1] + F.acnt[n - 1] - o0;
     for (uint32_t j = tid; j < total; j += nthr) {
@@ -323,6 +328,15 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
     }
     for (int v = tid; v < n; v += nthr) c_off[v] = F.aoff[v] - o0;
     if (tid == 0) c_off[n] = total;
+    __syncthreads();
+    // per node, the OR of the masks of the survivors before each one
+    for (int v = tid; v < n; v += nthr) {
+        uint64_t acc = 0ull;
+        for (uint32_t j = c_off[v]; j < c_off[v + 1]; ++j) {
+            c_orb[j] = acc;
+            acc |= c_mask[j];
+        }
+    }
 }
 
 __device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
@@ -332,13 +346,20 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
     const uint64_t* c_mask = (const uint64_t*)cache;
     const int64_t* c_key = (const int64_t*)(cache + 8 * (size_t)F.cap);
-    const uint32_t* c_rank = (const uint32_t*)(cache + 16 * (size_t)F.cap);
-    const uint32_t* c_off = (const uint32_t*)(cache + 20 * (size_t)F.cap);
+    const uint64_t* c_orb = (const uint64_t*)(cache + 16 * (size_t)F.cap);
+    const uint32_t* c_rank = (const uint32_t*)(cache + 24 * (size_t)F.cap);
+    const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)F.cap);
     for (int i = lane; i < n; i += 32) {
         W.ord[i] = S.cur_order[(size_t)c * n + i];
         W.rank[i] = S.cur_rank[(size_t)c * n + i];
         W.key[i] = S.cur_key[(size_t)c * n + i];
+        W.nkey[i] = W.key[i];
         W.since[i] = F.t0;
+        // the cache index of node i's current best survivor
+        uint32_t cj = 0;
+        if (F.staged)
+            for (cj = c_off[i]; cj + 1 < c_off[i + 1] && c_rank[cj] != W.rank[i]; ++cj) {}
+        W.cj[i] = cj;
     }
     __syncwarp();
     {
@@ -369,13 +390,20 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     for (int it = 0; it < F.iters; ++it) {
         const int64_t t = F.t0 + it;
         if ((it & 31) == 0) {
-            // the next 32 steps' Philox blocks, one per lane
+            // the next 32 steps' Philox blocks, one per lane, and what the MH test needs of
+            // them: u, and ln u within the FP32 log's error plus the rounding bound of the
+            // change (the test is decided outside [rlo, rhi])
             const U64x4 xr = philox4x64((uint64_t)(t + lane), (uint64_t)c, 0, 0, S.seed, 0);
+            const double u = __dmul_rn(__dadd_rn((double)(xr.x[1] >> 12), 0.5), 0x1p-52);
+            const float luf = logf((float)u);
+            const double mg = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
             W.rx0[lane] = xr.x[0];
-            W.rx1[lane] = xr.x[1];
+            W.ru[lane] = u;
+            W.rlo[lane] = (double)luf - mg;
+            W.rhi[lane] = (double)luf + mg;
             __syncwarp();
         }
-        const uint64_t x0 = W.rx0[it & 31], x1 = W.rx1[it & 31];
+        const uint64_t x0 = W.rx0[it & 31];
         int a, b;
         pair_decode(n, __umul64hi(x0, P), a, b);
         const int va = W.ord[a], vb = W.ord[b];
@@ -387,6 +415,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         uint32_t wj[2] = {0, 0}, wj1[2] = {0, 0};
         uint64_t wnpc[2] = {0, 0};
         bool act[2] = {false, false};
+        bool kept[2] = {false, false};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int p = lane + 32 * h;
@@ -394,10 +423,26 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
                 const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
                 wnpc[h] = ~compress_pred(excl, nd);
-                wj[h] = F.staged ? c_off[nd] : F.aoff[nd];
-                wj1[h] = F.staged ? c_off[nd + 1] : F.aoff[nd] + F.acnt[nd];
                 node[h] = nd;
-                act[h] = true;
+                if (F.staged) {
+                    // The node's best set so far is the first survivor consistent with its
+                    // old predecessors.  A survivor before it can only become consistent by
+                    // containing a gained predecessor; if none does, the answer is that set
+                    // again (still consistent) or lies after it.
+                    const uint64_t old_pred = (p == a) ? W.pre[b] : (p == b) ? W.pre[a] : W.pre[p];
+                    const uint64_t gained = compress_pred(excl & ~old_pred, nd);
+                    const uint32_t cj = W.cj[nd];
+                    const bool none_before = (c_orb[cj] & gained) == 0ull;
+                    const bool stays = (c_mask[cj] & wnpc[h]) == 0ull;
+                    wj[h] = none_before ? (stays ? cj : cj + 1) : c_off[nd];
+                    wj1[h] = c_off[nd + 1];
+                    kept[h] = none_before && stays;
+                    act[h] = !kept[h];
+                } else {
+                    wj[h] = F.aoff[nd];
+                    wj1[h] = F.aoff[nd] + F.acnt[nd];
+                    act[h] = true;
+                }
             }
         }
         // survivors of each node in score order: the first consistent one wins
@@ -405,7 +450,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         bool moved = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (!act[h]) continue;
+            if (!act[h] && !kept[h]) continue;
             const int nd = node[h];
             if (F.staged) {
                 nrank[h] = c_rank[wj[h]];
@@ -434,32 +479,21 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 if (node[h] >= 0) dpart += key_to_double(W.nkey[node[h]]) - key_to_double(W.key[node[h]]);
 #pragma unroll
             for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
-            // nodes of the span (their keys are in nkey)
-            uint64_t span = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (node[h] >= 0) span |= 1ull << node[h];
-            const uint32_t span_lo = __reduce_or_sync(0xffffffffu, (uint32_t)span);
-            const uint32_t span_hi = __reduce_or_sync(0xffffffffu, (uint32_t)(span >> 32));
-            const uint64_t spanm = ((uint64_t)span_hi << 32) | span_lo;
             acc = 0;
             if (lane == 0) {
-                const double u = __dmul_rn(__dadd_rn((double)(x1 >> 12), 0.5), 0x1p-52);
-                const float luf = logf((float)u);
+                const int q = it & 31;
                 const double xa = S.literal_log ? dpart : LN10 * dpart;
-                const double margin = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
-                const double gap = (double)luf - xa;
                 int exact = 0;
-                if (gap > margin) acc = 0;
-                else if (gap < -margin) { acc = 1; exact = 1; }
+                if (xa < W.rlo[q]) acc = 0;
+                else if (xa > W.rhi[q]) { acc = 1; exact = 1; }
                 else exact = 2;
                 if (exact) {
+                    // the proposal's keys: nkey holds the span's new keys and everyone else's
                     s2 = 0.0;
-                    for (int i = 0; i < n; ++i)
-                        s2 = __dadd_rn(s2, key_to_double(((spanm >> i) & 1) ? W.nkey[i] : W.key[i]));
+                    for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
                     if (exact == 2) {
                         const double delta = __dsub_rn(s2, score);
-                        const double lu = log(u);
+                        const double lu = log(W.ru[q]);
                         acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
                     }
                 }
@@ -468,6 +502,12 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             s2 = __shfl_sync(0xffffffffu, s2, 0);
         }
         // (not moved: no parent set changes, s' = s bit for bit and ln u < 0 accepts)
+        if (!acc) {
+            // the rejected proposal's keys: nkey equals key again outside any span
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (node[h] >= 0) W.nkey[node[h]] = W.key[node[h]];
+        }
         if (acc) {
             if (moved) {
 #pragma unroll
@@ -478,6 +518,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                         W.since[nd] = t;
                         W.rank[nd] = nrank[h];
                         W.key[nd] = W.nkey[nd];
+                        W.cj[nd] = wj[h];
                     }
                 }
             }
