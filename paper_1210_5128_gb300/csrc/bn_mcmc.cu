@@ -294,8 +294,10 @@ struct FusedSmem {
     int64_t nkey[MAXN];
     int64_t since[MAXN];
     uint64_t pre[MAXN];        // nodes at positions < p of the current order
-    uint32_t cj[MAXN];         // cache index of each node's current best survivor
-    uint64_t rx0[32];          // the next 32 steps: Philox x0 (the pair),
+    uint32_t cj[MAXN];         // cache index of each node's current best survivor,
+    uint64_t cmask[MAXN];      //   its candidate mask
+    uint64_t corb[MAXN];       //   and the OR of the masks of the node's survivors before it
+    uint8_t ra[32], rb[32];    // the next 32 steps: the swapped positions a < b,
     double ru[32];             //   the MH uniform from x1,
     double rlo[32], rhi[32];   //   and the fast test's thresholds ln u -/+ its margin
 };
@@ -357,8 +359,11 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         W.since[i] = F.t0;
         // the cache index of node i's current best survivor
         uint32_t cj = 0;
-        if (F.staged)
+        if (F.staged) {
             for (cj = c_off[i]; cj + 1 < c_off[i + 1] && c_rank[cj] != W.rank[i]; ++cj) {}
+            W.cmask[i] = c_mask[cj];
+            W.corb[i] = c_orb[cj];
+        }
         W.cj[i] = cj;
     }
     __syncwarp();
@@ -397,15 +402,16 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             const double u = __dmul_rn(__dadd_rn((double)(xr.x[1] >> 12), 0.5), 0x1p-52);
             const float luf = logf((float)u);
             const double mg = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
-            W.rx0[lane] = xr.x[0];
+            int pa, pb;
+            pair_decode(n, __umul64hi(xr.x[0], P), pa, pb);
+            W.ra[lane] = (uint8_t)pa;
+            W.rb[lane] = (uint8_t)pb;
             W.ru[lane] = u;
             W.rlo[lane] = (double)luf - mg;
             W.rhi[lane] = (double)luf + mg;
             __syncwarp();
         }
-        const uint64_t x0 = W.rx0[it & 31];
-        int a, b;
-        pair_decode(n, __umul64hi(x0, P), a, b);
+        const int a = W.ra[it & 31], b = W.rb[it & 31];
         const int va = W.ord[a], vb = W.ord[b];
         const uint64_t bva = 1ull << va, bvb = 1ull << vb;
         // the span a..b of the proposed order: its nodes and their predecessor sets (the
@@ -432,8 +438,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     const uint64_t old_pred = (p == a) ? W.pre[b] : (p == b) ? W.pre[a] : W.pre[p];
                     const uint64_t gained = compress_pred(excl & ~old_pred, nd);
                     const uint32_t cj = W.cj[nd];
-                    const bool none_before = (c_orb[cj] & gained) == 0ull;
-                    const bool stays = (c_mask[cj] & wnpc[h]) == 0ull;
+                    const bool none_before = (W.corb[nd] & gained) == 0ull;
+                    const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
                     wj[h] = none_before ? (stays ? cj : cj + 1) : c_off[nd];
                     wj1[h] = c_off[nd + 1];
                     kept[h] = none_before && stays;
@@ -519,6 +525,10 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                         W.rank[nd] = nrank[h];
                         W.key[nd] = W.nkey[nd];
                         W.cj[nd] = wj[h];
+                        if (F.staged) {
+                            W.cmask[nd] = c_mask[wj[h]];
+                            W.corb[nd] = c_orb[wj[h]];
+                        }
                     }
                 }
             }
