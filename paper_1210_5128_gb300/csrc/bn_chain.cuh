@@ -136,10 +136,11 @@ __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], c
 
 // rounding bound of the MH test's right-hand side: two sequential sums of n entries of
 // magnitude <= max_abs (each within (n - 1) 2^-53 n max_abs) and the change summed over
-// the re-scored nodes, times ln 10, with a factor 8 to spare
+// the re-scored nodes, times ln 10, with a factor 8 to spare; plus, for a change summed in
+// fixed point, its rounding (2n entries each within 2^-33), times ln 10 with a factor 2
 inline double mh_margin(int n, double max_abs)
 {
-    return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52;
+    return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52 + 2.0 * 2.31 * (double)n * 0x1p-32;
 }
 
 struct LearnedPath;                       // bn_learned.cu

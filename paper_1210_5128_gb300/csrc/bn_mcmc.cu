@@ -275,14 +275,17 @@ struct FusedArgs {
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
 };
 
-// shared-memory cache of a network's survivors: candidate mask, key, the OR of the masks of
-// the node's survivors before it, and rank of every survivor (score order), and the node
-// offsets
+// shared-memory cache of a network's survivors: candidate mask, the entry in 64-bit fixed
+// point (2^-32 units), the OR of the masks of the node's survivors before it, and rank of
+// every survivor (score order), and the node offsets
 __host__ __device__ constexpr size_t surv_cache_bytes(int cap)
 {
     return (size_t)cap * (8 + 8 + 8 + 4) + 4 * (MAXN + 1);
 }
 static constexpr int SURV_CAP_MAX = 2400;
+// cached networks sum entry changes in 64-bit fixed point (2^-32 units): entries below 2^22
+// in magnitude keep every sum of up to 2 x 64 changes inside int64
+static constexpr double FX_LIMIT = 4194304.0;
 
 static constexpr int FUSED_WARPS = 2;      // chains per block of one network's fused launch
 static constexpr int BATCH_WARPS = 8;      // chains per block of a many-network launch
@@ -297,10 +300,18 @@ struct FusedSmem {
     uint32_t cj[MAXN];         // cache index of each node's current best survivor,
     uint64_t cmask[MAXN];      //   its candidate mask
     uint64_t corb[MAXN];       //   and the OR of the masks of the node's survivors before it
+    int64_t fx[MAXN];          // each node's current entry in fixed point (cached networks)
     uint8_t ra[32], rb[32];    // the next 32 steps: the swapped positions a < b,
     double ru[32];             //   the MH uniform from x1,
     double rlo[32], rhi[32];   //   and the fast test's thresholds ln u -/+ its margin
 };
+
+// an entry (order-preserving key) in fixed point, 2^-32 units, rounded to nearest; exact
+// sums of these decide most MH tests (entries below 2^22 in magnitude, see FX_LIMIT)
+__device__ __forceinline__ int64_t entry_fx(int64_t key)
+{
+    return __double2ll_rn(key_to_double(key) * 4294967296.0);
+}
 
 // a network's survivors (mask, rank, key in score order; node offsets) into the block's
 // shared-memory cache, by all `nthr` threads of the block
@@ -309,7 +320,7 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
 {
     const int n = S.n;
     uint64_t* c_mask = (uint64_t*)cache;
-    int64_t* c_key = (int64_t*)(cache + 8 * (size_t)F.cap);
+    int64_t* c_fx = (int64_t*)(cache + 8 * (size_t)F.cap);
     uint64_t* c_orb = (uint64_t*)(cache + 16 * (size_t)F.cap);
     uint32_t* c_rank = (uint32_t*)(cache + 24 * (size_t)F.cap);
     uint32_t* c_off = (uint32_t*)(cache + 28 * (size_t)F.cap);
@@ -326,7 +337,7 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
         const uint32_t r = S.srank[(size_t)lo * S.Sp + F.aspos[o0 + j]];
         c_mask[j] = F.amask[o0 + j];
         c_rank[j] = r;
-        c_key[j] = S.keys[(size_t)lo * S.Sp + r];
+        c_fx[j] = entry_fx(S.keys[(size_t)lo * S.Sp + r]);
     }
     for (int v = tid; v < n; v += nthr) c_off[v] = F.aoff[v] - o0;
     if (tid == 0) c_off[n] = total;
@@ -347,7 +358,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     const int n = S.n;
     const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
     const uint64_t* c_mask = (const uint64_t*)cache;
-    const int64_t* c_key = (const int64_t*)(cache + 8 * (size_t)F.cap);
+    const int64_t* c_fx = (const int64_t*)(cache + 8 * (size_t)F.cap);
     const uint64_t* c_orb = (const uint64_t*)(cache + 16 * (size_t)F.cap);
     const uint32_t* c_rank = (const uint32_t*)(cache + 24 * (size_t)F.cap);
     const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)F.cap);
@@ -363,6 +374,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             for (cj = c_off[i]; cj + 1 < c_off[i + 1] && c_rank[cj] != W.rank[i]; ++cj) {}
             W.cmask[i] = c_mask[cj];
             W.corb[i] = c_orb[cj];
+            W.fx[i] = c_fx[cj];
         }
         W.cj[i] = cj;
     }
@@ -454,13 +466,15 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         // survivors of each node in score order: the first consistent one wins
         span_walk(F.staged ? c_mask : F.amask, wj, wj1, wnpc, act, lane);
         bool moved = false;
+        int64_t nfx[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (!act[h] && !kept[h]) continue;
             const int nd = node[h];
             if (F.staged) {
+                // the new key is fetched only if the exact test needs it
                 nrank[h] = c_rank[wj[h]];
-                W.nkey[nd] = c_key[wj[h]];
+                nfx[h] = c_fx[wj[h]];
             } else {
                 nrank[h] = S.srank[(size_t)nd * S.Sp + F.aspos[wj[h]]];
                 W.nkey[nd] = S.keys[(size_t)nd * S.Sp + nrank[h]];
@@ -475,33 +489,58 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             __syncwarp();
             // MH test.  The exact test compares ln u with ln10 (s' - s), s' the FP64 sum over
             // nodes in ascending id.  Most steps are decided without it: the change of the
-            // re-scored nodes alone (any summation order) is within ~n eps sum|entries| of
-            // s' - s and an FP32 log(u) within 1e-6 (1 + |ln u|) of ln u; when the two sides
+            // re-scored nodes alone (exact in fixed point for cached networks, within n 2^-32
+            // of the true change; an FP64 sum in any order otherwise) is within the margin of
+            // s' - s, and an FP32 log(u) within 1e-6 (1 + |ln u|) of ln u; when the two sides
             // are farther apart than both errors the decision is the exact one.  Close calls
-            // and accepted moves (whose new score the state keeps) take the exact path.
-            double dpart = 0.0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (node[h] >= 0) dpart += key_to_double(W.nkey[node[h]]) - key_to_double(W.key[node[h]]);
-#pragma unroll
-            for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
+            // and accepted moves (whose new score the state keeps) take the exact path, which
+            // fetches the span's new FP64 entries.
+            int exact = 0;
             acc = 0;
-            if (lane == 0) {
-                const int q = it & 31;
-                const double xa = S.literal_log ? dpart : LN10 * dpart;
-                int exact = 0;
-                if (xa < W.rlo[q]) acc = 0;
-                else if (xa > W.rhi[q]) { acc = 1; exact = 1; }
-                else exact = 2;
+            if (F.staged) {
+                long long dfx = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (node[h] >= 0) dfx += nfx[h] - W.fx[node[h]];
+#pragma unroll
+                for (int off = 16; off; off >>= 1) dfx += __shfl_down_sync(0xffffffffu, dfx, off);
+                if (lane == 0) {
+                    const double dpart = (double)dfx * 0x1p-32;
+                    const double xa = S.literal_log ? dpart : LN10 * dpart;
+                    const int q = it & 31;
+                    exact = xa < W.rlo[q] ? 0 : (xa > W.rhi[q] ? 1 : 2);
+                }
+                exact = __shfl_sync(0xffffffffu, exact, 0);
                 if (exact) {
-                    // the proposal's keys: nkey holds the span's new keys and everyone else's
-                    s2 = 0.0;
-                    for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
-                    if (exact == 2) {
-                        const double delta = __dsub_rn(s2, score);
-                        const double lu = log(W.ru[q]);
-                        acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
-                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (node[h] >= 0) W.nkey[node[h]] = S.keys[(size_t)node[h] * S.Sp + nrank[h]];
+                    __syncwarp();
+                }
+            } else {
+                double dpart = 0.0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (node[h] >= 0) dpart += key_to_double(W.nkey[node[h]]) - key_to_double(W.key[node[h]]);
+#pragma unroll
+                for (int off = 16; off; off >>= 1) dpart += __shfl_down_sync(0xffffffffu, dpart, off);
+                if (lane == 0) {
+                    const double xa = S.literal_log ? dpart : LN10 * dpart;
+                    const int q = it & 31;
+                    exact = xa < W.rlo[q] ? 0 : (xa > W.rhi[q] ? 1 : 2);
+                }
+                exact = __shfl_sync(0xffffffffu, exact, 0);
+            }
+            if (lane == 0 && exact) {
+                // the proposal's keys: nkey holds the span's new keys and everyone else's
+                s2 = 0.0;
+                for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+                if (exact == 2) {
+                    const double delta = __dsub_rn(s2, score);
+                    const double lu = log(W.ru[it & 31]);
+                    acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+                } else {
+                    acc = 1;
                 }
             }
             acc = __shfl_sync(0xffffffffu, acc, 0);
@@ -528,6 +567,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                         if (F.staged) {
                             W.cmask[nd] = c_mask[wj[h]];
                             W.corb[nd] = c_orb[wj[h]];
+                            W.fx[nd] = nfx[h];
                         }
                     }
                 }
@@ -886,7 +926,7 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     F.acnt = ch->t->acnt;
     F.t0 = t0;
     F.iters = iters;
-    F.staged = ch->t->alive_total <= SURV_CAP_MAX ? 1 : 0;
+    F.staged = ch->t->alive_total <= SURV_CAP_MAX && ch->t->max_abs_survivor < FX_LIMIT ? 1 : 0;
     F.cap = F.staged ? (int)ch->t->alive_total : 0;
     F.margin_x = mh_margin(ch->S.n, ch->t->max_abs_survivor);
     size_t smem = 0;
@@ -1435,7 +1475,8 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
     const unsigned blocks = (unsigned)base[nf];
     int cap = 0;
     for (bn_chains* c : fused)
-        if (c->t->alive_total <= SURV_CAP_MAX) cap = std::max(cap, (int)c->t->alive_total);
+        if (c->t->alive_total <= SURV_CAP_MAX && c->t->max_abs_survivor < FX_LIMIT)
+            cap = std::max(cap, (int)c->t->alive_total);
     size_t smem = 0;
     {
         int rc = fused_smem_setup(cap, &smem);
@@ -1457,7 +1498,7 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
             f.acnt = t->acnt;
             f.t0 = fused[i]->steps + done;
             f.iters = it;
-            f.staged = t->alive_total <= cap ? 1 : 0;
+            f.staged = t->alive_total <= cap && t->max_abs_survivor < FX_LIMIT ? 1 : 0;
             f.cap = cap;
             f.margin_x = mh_margin(t->n, t->max_abs_survivor);
             hit[(size_t)l * nf + i] = it;
