@@ -121,6 +121,7 @@ struct BuildArgs {
     int64_t S, Sp;
     int units_per_node;
     int cells_cap;
+    int cells_max;           // largest histogram (q * r) of any entry
     const uint8_t* arity;
     const double* ppf;        // n*n or null
     double log10g;
@@ -334,10 +335,14 @@ struct Temps {
     }
 };
 
+// Counting: plain shared-memory atomics, except for tiny histograms (<= 8 cells), where
+// the lanes of a warp collide on a few cells and warp-aggregated adds (one atomic per
+// distinct cell, __match_any_sync) win.  Measured on GB300 at n = 60, k = 4, m = 1000
+// (243-cell histograms): 0.070 s plain against 0.224 s aggregated for the whole table.
 template <int KT>
 static int launch_build_kt(const BuildArgs& A, bool smem_data, size_t smem, int grid, cudaStream_t s)
 {
-    const bool agg = getenv("BN_BUILD_PLAIN_ATOMICS") == nullptr;
+    const bool agg = A.cells_max <= 8;
     if (smem_data) {
         if (agg) {
             cudaFuncSetAttribute(k_build<KT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -534,6 +539,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     A.Sp = t->Sp;
     A.units_per_node = (int)((S + BUILD_RANGE - 1) / BUILD_RANGE);
     A.cells_cap = (int)round_up(cells_max, 32);
+    A.cells_max = (int)cells_max;
     A.arity = d_ar;
     A.ppf = d_ppf;
     A.log10g = log10g;
