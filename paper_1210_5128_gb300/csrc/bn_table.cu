@@ -137,6 +137,22 @@ struct BuildArgs {
 // state) counts over all m rows, then the lgamma terms summed exactly in 128-bit fixed
 // point (the sum is independent of the cell order), one rounding to FP64, the
 // structure penalty, and the prior terms in ascending parent id.
+// an entry from its exact lgamma sum: / ln 10, the size penalty, the prior of every
+// parent (candidate mask -> node ids, ascending), as one FP64 value in key form
+__device__ __forceinline__ void finish_entry(const BuildArgs& A, int i, fx128 acc, int j, uint64_t mask, int64_t rho)
+{
+    double ls = __dadd_rn(__ddiv_rn(fx_to_double(acc), LN10), __dmul_rn((double)j, A.log10g));
+    if (A.ppf) {
+        uint64_t mm = mask;
+        while (mm) {
+            const int c = __ffsll((long long)mm) - 1;
+            mm &= mm - 1;
+            ls = __dadd_rn(ls, A.ppf[(size_t)i * A.n + c + (c >= i ? 1 : 0)]);
+        }
+    }
+    A.keys[(size_t)i * A.Sp + rho] = double_to_key(ls);
+}
+
 template <int KT, bool SMEM_DATA, bool WARP_AGG>
 __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
 {
@@ -161,6 +177,10 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
         int j;
         uint64_t mask;
         unrank_dev(N, r0, j, mask);
+        fx128 my_acc = 0;
+        int my_j = 0;
+        uint64_t my_mask = 0;
+        int64_t my_rho = 0;
         for (int64_t rho = r0; rho < r1; ++rho) {
             int par[KT], stride[KT];
             int q = 1;
@@ -179,6 +199,9 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
                 }
             }
             const int cells = q * ri;
+            int cstride[KT];                 // cell = child state + sum of parent states x these
+#pragma unroll
+            for (int t = 0; t < KT; ++t) cstride[t] = stride[t] * ri;
             for (int c = lane; c < cells; c += 32) hist[c] = 0u;
             __syncwarp();
             for (int w = lane; w < A.mw; w += 32) {
@@ -198,12 +221,21 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
                         const unsigned grp = __match_any_sync(act, cell);
                         if (live && (__ffs(grp) - 1) == lane) atomicAdd(&hist[cell], (uint32_t)__popc(grp));
                     }
+                } else if (nrows == 16) {
+                    // a full word: 16 rows with constant shifts
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) {
+                        int cell = (int)((cw >> (2 * b)) & 3u);
+#pragma unroll
+                        for (int t = 0; t < KT; ++t) cell += (int)((pw[t] >> (2 * b)) & 3u) * cstride[t];
+                        atomicAdd(&hist[cell], 1u);
+                    }
                 } else {
                     for (int b = 0; b < nrows; ++b) {
-                        int cfg = 0;
+                        int cell = (int)((cw >> (2 * b)) & 3u);
 #pragma unroll
-                        for (int t = 0; t < KT; ++t) cfg += (int)((pw[t] >> (2 * b)) & 3u) * stride[t];
-                        atomicAdd(&hist[cfg * ri + (int)((cw >> (2 * b)) & 3u)], 1u);
+                        for (int t = 0; t < KT; ++t) cell += (int)((pw[t] >> (2 * b)) & 3u) * cstride[t];
+                        atomicAdd(&hist[cell], 1u);
                     }
                 }
             }
@@ -227,15 +259,18 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
                 hi = __shfl_xor_sync(0xffffffffu, hi, off);
                 acc += ((fx128)hi << 64) | (fx128)lo;
             }
-            if (lane == 0) {
-                double s = fx_to_double(acc);
-                double ls = __dadd_rn(__ddiv_rn(s, LN10), __dmul_rn((double)j, A.log10g));
-                if (A.ppf) {
-#pragma unroll
-                    for (int t = 0; t < KT; ++t)
-                        if (t < j) ls = __dadd_rn(ls, A.ppf[(size_t)i * A.n + par[t]]);
-                }
-                A.keys[(size_t)i * A.Sp + rho] = double_to_key(ls);
+            // every lane holds the sum; lane (rho - r0) % 32 finishes this entry, 32 entries
+            // at a time (the FP64 tail runs on all lanes instead of on one)
+            const int slot = (int)((rho - r0) & 31);
+            if (lane == slot) {
+                my_acc = acc;
+                my_j = j;
+                my_mask = mask;
+                my_rho = rho;
+            }
+            if (slot == 31 || rho + 1 == r1) {
+                if (lane <= slot) finish_entry(A, i, my_acc, my_j, my_mask, my_rho);
+                __syncwarp();
             }
             __syncwarp();
             next_set(N, j, mask);
