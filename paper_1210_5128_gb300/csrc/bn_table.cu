@@ -48,8 +48,10 @@ __device__ __forceinline__ void next_set(int N, int& j, uint64_t& mask)
 }
 
 // ---------------------------------------------------------------------------------
-// a1: data staging.  m x n row-major uint8 -> [n][mw] words of 16 two-bit values
-// (row 16w + b at bits 2b..2b+1); checks data[r][i] < arity[i].
+// a1: data staging.  m x n row-major uint8 -> [n][mw] words of 16 two-bit values.  Row
+// 16w + b sits at bits 8(b & 3) + 2(b >> 2), so one shift by 2s and a mask 0x03030303
+// yields rows 16w + 4s .. 16w + 4s + 3 as four bytes.  Rows past m are 0 (every variable
+// in state 0); the counting kernel takes their number back out of cell 0.
 // ---------------------------------------------------------------------------------
 __global__ void k_pack(const uint8_t* __restrict__ data, int m, int n, int mw,
                        const uint8_t* __restrict__ arity, uint32_t* __restrict__ packed,
@@ -66,7 +68,7 @@ __global__ void k_pack(const uint8_t* __restrict__ data, int m, int n, int mw,
         if (row < m) {
             uint32_t x = data[(size_t)row * n + v];
             if (x >= (uint32_t)av) { bad = true; x = 0; }   // never let a bad value index a count table
-            word |= x << (2 * b);
+            word |= x << (8 * (b & 3) + 2 * (b >> 2));
         }
     }
     if (bad) atomicOr(status, STATUS_BADINPUT);
@@ -132,11 +134,6 @@ struct BuildArgs {
     int64_t* keys;
 };
 
-// a2 + a3: one warp per work unit of BUILD_RANGE consecutive ranks of one node.  Per
-// parent set: a warp-private shared-memory histogram of (parent configuration, child
-// state) counts over all m rows, then the lgamma terms summed exactly in 128-bit fixed
-// point (the sum is independent of the cell order), one rounding to FP64, the
-// structure penalty, and the prior terms in ascending parent id.
 // an entry from its exact lgamma sum: / ln 10, the size penalty, the prior of every
 // parent (candidate mask -> node ids, ascending), as one FP64 value in key form
 __device__ __forceinline__ void finish_entry(const BuildArgs& A, int i, fx128 acc, int j, uint64_t mask, int64_t rho)
@@ -153,20 +150,97 @@ __device__ __forceinline__ void finish_entry(const BuildArgs& A, int i, fx128 ac
     A.keys[(size_t)i * A.Sp + rho] = double_to_key(ls);
 }
 
+// Counts of one packed word (16 rows).  cell = child state + sum_t parent state_t * cs[t];
+// with cells <= 256 four rows' cells are formed at once as the bytes of one 32-bit
+// integer (no byte can carry: each is a cell index < 256), otherwise two rows' as 16-bit
+// halves.  Parents past the set's size have cs = 0.
+template <int KT, bool WARP_AGG>
+__device__ __forceinline__ void count_word(uint32_t* hist, uint32_t cw, const uint32_t (&pw)[KT],
+                                           const uint32_t (&cs)[KT], bool bytes, int lane)
+{
+    if (bytes) {
+#pragma unroll
+        for (int sft = 0; sft < 8; sft += 2) {
+            uint32_t c4 = (cw >> sft) & 0x03030303u;
+#pragma unroll
+            for (int t = 0; t < KT; ++t) c4 += ((pw[t] >> sft) & 0x03030303u) * cs[t];
+            if (WARP_AGG) {
+                // tiny histograms: one add per distinct cell of the warp
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t cell = (c4 >> (8 * r)) & 0xffu;
+                    const unsigned grp = __match_any_sync(__activemask(), cell);
+                    if ((__ffs(grp) - 1) == lane) atomicAdd(&hist[cell], (uint32_t)__popc(grp));
+                }
+            } else {
+                atomicAdd(&hist[c4 & 0xffu], 1u);
+                atomicAdd(&hist[(c4 >> 8) & 0xffu], 1u);
+                atomicAdd(&hist[(c4 >> 16) & 0xffu], 1u);
+                atomicAdd(&hist[c4 >> 24], 1u);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 16; h += 8) {
+#pragma unroll
+            for (int sft = 0; sft < 8; sft += 2) {
+                uint32_t c2 = (cw >> (h + sft)) & 0x00030003u;
+#pragma unroll
+                for (int t = 0; t < KT; ++t) c2 += ((pw[t] >> (h + sft)) & 0x00030003u) * cs[t];
+                atomicAdd(&hist[c2 & 0xffffu], 1u);
+                atomicAdd(&hist[c2 >> 16], 1u);
+            }
+        }
+    }
+}
+
+// The lgamma terms of one count table: per configuration c, sum_x L_cell[N_cx] -
+// L_cfg[sum_x N_cx], exactly in 128-bit fixed point.  Every cell read is set back to 0,
+// so the warp's histogram is all zero again for the next entry.
+template <int RI>
+__device__ __forceinline__ fx128 score_cells(uint32_t* hist, int q, const fx128* __restrict__ Lx,
+                                             const fx128* __restrict__ Lc, int lane)
+{
+    fx128 acc = 0;
+    for (int c = lane; c < q; c += 32) {
+        uint32_t v[RI], Nc = 0;
+#pragma unroll
+        for (int x = 0; x < RI; ++x) {
+            v[x] = hist[c * RI + x];
+            Nc += v[x];
+        }
+#pragma unroll
+        for (int x = 0; x < RI; ++x) {
+            hist[c * RI + x] = 0u;
+            acc += Lx[v[x]];
+        }
+        acc -= Lc[Nc];
+    }
+    return acc;
+}
+
+// a2 + a3: one warp per work unit of BUILD_RANGE consecutive ranks of one node.  Per
+// parent set: a warp-private shared-memory histogram of (parent configuration, child
+// state) counts over all m rows, then the lgamma terms summed exactly in 128-bit fixed
+// point (the sum is independent of the cell order), one rounding to FP64, the
+// structure penalty, and the prior terms in ascending parent id.
+// Shared memory holds the warps' histograms, then (when it fits) the packed data.
 template <int KT, bool SMEM_DATA, bool WARP_AGG>
 __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int data_words = A.n * A.mw;
+    uint32_t* hist = sm + warp * A.cells_cap;
     const uint32_t* D = A.packed;
-    uint32_t* hist = sm + (SMEM_DATA ? data_words : 0) + warp * A.cells_cap;
+    for (int c = lane; c < A.cells_cap; c += 32) hist[c] = 0u;
     if (SMEM_DATA) {
-        for (int t = threadIdx.x; t < data_words; t += blockDim.x) sm[t] = A.packed[t];
-        __syncthreads();
-        D = sm;
+        uint32_t* sd = sm + nw * A.cells_cap;
+        for (int t = threadIdx.x; t < A.n * A.mw; t += blockDim.x) sd[t] = A.packed[t];
+        D = sd;
     }
+    __syncthreads();
     const int N = A.n - 1;
+    const uint32_t pad = (uint32_t)(16 * A.mw - A.m);   // zero rows of the last word, all in cell 0
     const int64_t units = (int64_t)A.n * A.units_per_node;
     for (int64_t u = (int64_t)blockIdx.x * nw + warp; u < units; u += (int64_t)gridDim.x * nw) {
         const int i = (int)(u / A.units_per_node);
@@ -182,76 +256,39 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
         uint64_t my_mask = 0;
         int64_t my_rho = 0;
         for (int64_t rho = r0; rho < r1; ++rho) {
-            int par[KT], stride[KT];
+            int poff[KT];
+            uint32_t cs[KT];
             int q = 1;
             uint64_t mm = mask;
 #pragma unroll
             for (int t = 0; t < KT; ++t) {
-                par[t] = 0;
-                stride[t] = 0;
+                poff[t] = 0;
+                cs[t] = 0u;
                 if (t < j) {
-                    int c = __ffsll((long long)mm) - 1;
+                    const int c = __ffsll((long long)mm) - 1;
                     mm &= mm - 1;
-                    int p = c + (c >= i ? 1 : 0);
-                    par[t] = p;
-                    stride[t] = q;
-                    q *= A.arity[p];
+                    const int p = c + (c >= i ? 1 : 0);
+                    poff[t] = p * A.mw;
+                    cs[t] = (uint32_t)(q * ri);
+                    q *= __ldg(&A.arity[p]);
                 }
             }
-            const int cells = q * ri;
-            int cstride[KT];                 // cell = child state + sum of parent states x these
-#pragma unroll
-            for (int t = 0; t < KT; ++t) cstride[t] = stride[t] * ri;
-            for (int c = lane; c < cells; c += 32) hist[c] = 0u;
-            __syncwarp();
+            const bool bytes = q * ri <= 256;
             for (int w = lane; w < A.mw; w += 32) {
                 const uint32_t cw = Di[w];
                 uint32_t pw[KT];
 #pragma unroll
-                for (int t = 0; t < KT; ++t) pw[t] = (t < j) ? D[(size_t)par[t] * A.mw + w] : 0u;
-                const int nrows = min(16, A.m - 16 * w);
-                if (WARP_AGG) {
-                    for (int b = 0; b < 16; ++b) {
-                        const bool live = b < nrows;
-                        int cfg = 0;
-#pragma unroll
-                        for (int t = 0; t < KT; ++t) cfg += (int)((pw[t] >> (2 * b)) & 3u) * stride[t];
-                        const int cell = live ? cfg * ri + (int)((cw >> (2 * b)) & 3u) : -1;
-                        const unsigned act = __activemask();
-                        const unsigned grp = __match_any_sync(act, cell);
-                        if (live && (__ffs(grp) - 1) == lane) atomicAdd(&hist[cell], (uint32_t)__popc(grp));
-                    }
-                } else if (nrows == 16) {
-                    // a full word: 16 rows with constant shifts
-#pragma unroll
-                    for (int b = 0; b < 16; ++b) {
-                        int cell = (int)((cw >> (2 * b)) & 3u);
-#pragma unroll
-                        for (int t = 0; t < KT; ++t) cell += (int)((pw[t] >> (2 * b)) & 3u) * cstride[t];
-                        atomicAdd(&hist[cell], 1u);
-                    }
-                } else {
-                    for (int b = 0; b < nrows; ++b) {
-                        int cell = (int)((cw >> (2 * b)) & 3u);
-#pragma unroll
-                        for (int t = 0; t < KT; ++t) cell += (int)((pw[t] >> (2 * b)) & 3u) * cstride[t];
-                        atomicAdd(&hist[cell], 1u);
-                    }
-                }
+                for (int t = 0; t < KT; ++t) pw[t] = D[poff[t] + w];
+                count_word<KT, WARP_AGG>(hist, cw, pw, cs, bytes, lane);
             }
             __syncwarp();
+            if (lane == 0 && pad) hist[0] -= pad;
             const fx128* Lx = A.lut + (size_t)A.cell_lut[q * 5 + ri] * A.lut_stride;
             const fx128* Lc = A.lut + (size_t)A.cfg_lut[q * 5 + ri] * A.lut_stride;
-            fx128 acc = 0;
-            for (int c = lane; c < q; c += 32) {
-                uint32_t Nc = 0;
-                for (int x = 0; x < ri; ++x) {
-                    uint32_t v = hist[c * ri + x];
-                    Nc += v;
-                    acc += Lx[v];
-                }
-                acc -= Lc[Nc];
-            }
+            fx128 acc;
+            if (ri == 2) acc = score_cells<2>(hist, q, Lx, Lc, lane);
+            else if (ri == 3) acc = score_cells<3>(hist, q, Lx, Lc, lane);
+            else acc = score_cells<4>(hist, q, Lx, Lc, lane);
 #pragma unroll
             for (int off = 16; off; off >>= 1) {
                 uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
@@ -587,7 +624,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     size_t data_bytes = sizeof(uint32_t) * (size_t)n * mw;
     size_t hist_bytes = sizeof(uint32_t) * (size_t)A.cells_cap * nwarps;
     bool smem_data = data_bytes + hist_bytes <= 160 * 1024;
-    size_t smem = hist_bytes + (smem_data ? data_bytes : 0);
+    size_t smem = hist_bytes + (smem_data ? data_bytes : 0);   // histograms, then the data
     int per_sm = std::max(1, std::min(8, (int)((220 * 1024) / std::max<size_t>(smem + 1024, 1))));
     int64_t units = (int64_t)n * A.units_per_node;
     int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, (units + nwarps - 1) / nwarps);
