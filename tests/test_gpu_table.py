@@ -31,14 +31,18 @@ def test_table_every_entry_n20_with_prior(gpu):
     _cmp(gpu.table_scores(t), oracle.build_table(data, arity, k, R=R))
 
 
+@pytest.mark.parametrize("k", [3, 4])
 @pytest.mark.parametrize("m", [0, 1, 15, 16, 17, 333])
-def test_table_ragged_rows_and_mixed_arity(gpu, m):
+def test_table_ragged_rows_and_mixed_arity(gpu, m, k):
+    # m around the 16-row word (rows past m are zero and come out of cell 0); at k = 4 the
+    # count tables reach 4 * 4 * 4 * 3 * 3 = 576 cells, so entries above 256 cells take the
+    # 16-bit lanes and the rest the byte lanes in the same launch
     rng = np.random.default_rng(m)
     arity = np.array([2, 3, 4, 2, 4, 3, 2], np.uint8)
     data = np.stack([rng.integers(0, a, m) for a in arity], 1).astype(np.uint8).reshape(m, 7)
     for kind in (0, 1):
-        t = gpu.build_scores(data, arity, 3, score_kind=kind, ess=2.5, log10_gamma=-0.25)
-        _cmp(gpu.table_scores(t), oracle.build_table(data, arity, 3, kind, 2.5, -0.25))
+        t = gpu.build_scores(data, arity, k, score_kind=kind, ess=2.5, log10_gamma=-0.25)
+        _cmp(gpu.table_scores(t), oracle.build_table(data, arity, k, kind, 2.5, -0.25))
 
 
 @pytest.mark.parametrize("k", [0, 1, 5])
