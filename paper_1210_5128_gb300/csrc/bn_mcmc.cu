@@ -303,7 +303,8 @@ struct FusedSmem {
     int64_t fx[MAXN];          // each node's current entry in fixed point (cached networks)
     uint8_t ra[32], rb[32];    // the next 32 steps: the swapped positions a < b,
     double ru[32];             //   the MH uniform from x1,
-    double rlo[32], rhi[32];   //   and the fast test's thresholds ln u -/+ its margin
+    int64_t tlo[32], thi[32];  //   and the fast test's thresholds (ln u -/+ its margin) in
+                               //   the fixed-point units of the change, 2^-32 of a score
 };
 
 // an entry (order-preserving key) in fixed point, 2^-32 units, rounded to nearest; exact
@@ -409,18 +410,22 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         if ((it & 31) == 0) {
             // the next 32 steps' Philox blocks, one per lane, and what the MH test needs of
             // them: u, and ln u within the FP32 log's error plus the rounding bound of the
-            // change (the test is decided outside [rlo, rhi])
+            // change, divided by ln 10 (the test's factor) and scaled to the change's
+            // fixed-point units, one unit further out on each side than the conversion's
+            // rounding needs (the fast test is decided outside [tlo, thi] by two integer
+            // compares; the FP64 work runs here, once per 32 steps, in all lanes at once)
             const U64x4 xr = philox4x64((uint64_t)(t + lane), (uint64_t)c, 0, 0, S.seed, 0);
             const double u = __dmul_rn(__dadd_rn((double)(xr.x[1] >> 12), 0.5), 0x1p-52);
             const float luf = logf((float)u);
             const double mg = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
+            const double to_fx = S.literal_log ? 4294967296.0 : 4294967296.0 / LN10;
             int pa, pb;
             pair_decode(n, __umul64hi(xr.x[0], P), pa, pb);
             W.ra[lane] = (uint8_t)pa;
             W.rb[lane] = (uint8_t)pb;
             W.ru[lane] = u;
-            W.rlo[lane] = (double)luf - mg;
-            W.rhi[lane] = (double)luf + mg;
+            W.tlo[lane] = (int64_t)floor(((double)luf - mg) * to_fx) - 1;
+            W.thi[lane] = (int64_t)ceil(((double)luf + mg) * to_fx) + 1;
             __syncwarp();
         }
         const int a = W.ra[it & 31], b = W.rb[it & 31];
@@ -503,14 +508,11 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 for (int h = 0; h < 2; ++h)
                     if (node[h] >= 0) dfx += nfx[h] - W.fx[node[h]];
 #pragma unroll
-                for (int off = 16; off; off >>= 1) dfx += __shfl_down_sync(0xffffffffu, dfx, off);
-                if (lane == 0) {
-                    const double dpart = (double)dfx * 0x1p-32;
-                    const double xa = S.literal_log ? dpart : LN10 * dpart;
+                for (int off = 16; off; off >>= 1) dfx += __shfl_xor_sync(0xffffffffu, dfx, off);
+                {
                     const int q = it & 31;
-                    exact = xa < W.rlo[q] ? 0 : (xa > W.rhi[q] ? 1 : 2);
+                    exact = dfx < W.tlo[q] ? 0 : (dfx > W.thi[q] ? 1 : 2);     // equal in every lane
                 }
-                exact = __shfl_sync(0xffffffffu, exact, 0);
                 if (exact) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
@@ -527,7 +529,10 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 if (lane == 0) {
                     const double xa = S.literal_log ? dpart : LN10 * dpart;
                     const int q = it & 31;
-                    exact = xa < W.rlo[q] ? 0 : (xa > W.rhi[q] ? 1 : 2);
+                    // the thresholds back in ln units (a little further out than ln u -/+ the
+                    // margin, so still sound for this FP64 change)
+                    const double back = S.literal_log ? 0x1p-32 : LN10 * 0x1p-32;
+                    exact = xa < (double)W.tlo[q] * back ? 0 : (xa > (double)W.thi[q] * back ? 1 : 2);
                 }
                 exact = __shfl_sync(0xffffffffu, exact, 0);
             }
