@@ -2,6 +2,8 @@
 // uniform-proposal sampler (bn_mcmc.cu) and the learned-proposal sampler (bn_learned.cu).
 #pragma once
 
+#include <cmath>
+
 #include "bn_mlp.cuh"
 #include "bn_table.cuh"
 
@@ -141,6 +143,18 @@ __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], c
 inline double mh_margin(int n, double max_abs)
 {
     return 8.0 * 2.31 * (double)(n + 8) * (double)n * max_abs * 0x1p-52 + 2.0 * 2.31 * (double)n * 0x1p-32;
+}
+
+// Guard of fixed-point order-score comparisons, in 2^-32 units: an order score summed left
+// to right in FP64 from n entries of magnitude <= max_abs is within (n-1) 2^-53 n max_abs
+// (x 1.01) of the exact sum, and the sum of the entries rounded to 2^-32 within n 2^-33 of
+// it; G bounds both in 2^-32 units, and two scores whose fixed-point sums differ by more
+// than 2G + 1 compare the same way in FP64.  One unit to spare.
+inline int64_t score_guard_fx(int n, double max_abs)
+{
+    const double g = (1.01 * (double)(n - 1) * (double)n * max_abs * 0x1p-53 + (double)n * 0x1p-33) * 0x1p32;
+    const int64_t G = (int64_t)std::ceil(g) + 1;
+    return 2 * G + 2;
 }
 
 struct LearnedPath;                       // bn_learned.cu

@@ -273,6 +273,8 @@ struct FusedArgs {
     int staged;          // 1: the network's survivors fit the warp's shared-memory cache
     int cap;             // survivors per warp cache (shared-memory layout of the launch)
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
+    int64_t guard_fx;    // two order scores whose exact fixed-point sums differ by more than
+                         // this (2^-32 units) compare the same way as their FP64 sums
 };
 
 // shared-memory cache of a network's survivors: candidate mask, the entry in 64-bit fixed
@@ -305,7 +307,45 @@ struct FusedSmem {
     double ru[32];             //   the MH uniform from x1,
     int64_t tlo[32], thi[32];  //   and the fast test's thresholds (ln u -/+ its margin) in
                                //   the fixed-point units of the change, 2^-32 of a score
+    uint32_t brank[MAXN];      // ranks of the best state so far
+    uint8_t kst[MAXN];         // 1: key[i] (and nkey[i]) not yet read for the node's rank
 };
+
+// Cached networks leave the FP64 order score of an accepted move for later when the fast
+// test already decided it (the exact fixed-point sum tracks the state); these recover it.
+// Keys of nodes whose parent set changed in such moves, read for their ranks:
+__device__ __forceinline__ void refresh_keys(const ChainState& S, FusedSmem& W, int n, int lane)
+{
+    for (int i = lane; i < n; i += 32)
+        if (W.kst[i]) {
+            const int64_t k = S.keys[(size_t)i * S.Sp + W.rank[i]];
+            W.key[i] = k;
+            W.nkey[i] = k;
+            W.kst[i] = 0;
+        }
+    __syncwarp();
+}
+// the FP64 order score: entries in ascending node id, summed left to right (lane 0)
+__device__ __forceinline__ double seq_score(const int64_t* k, int n, int lane)
+{
+    double s = 0.0;
+    if (lane == 0)
+        for (int i = 0; i < n; ++i) s = __dadd_rn(s, key_to_double(k[i]));
+    return __shfl_sync(0xffffffffu, s, 0);
+}
+// the same for the best state, from its ranks
+__device__ __forceinline__ double best_score_of(const ChainState& S, const FusedSmem& W, int n, int lane)
+{
+    int64_t k0 = 0, k1 = 0;
+    if (lane < n) k0 = S.keys[(size_t)lane * S.Sp + W.brank[lane]];
+    if (lane + 32 < n) k1 = S.keys[(size_t)(lane + 32) * S.Sp + W.brank[lane + 32]];
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t v = __shfl_sync(0xffffffffu, i < 32 ? k0 : k1, i & 31);
+        if (lane == 0) s = __dadd_rn(s, key_to_double(v));
+    }
+    return __shfl_sync(0xffffffffu, s, 0);
+}
 
 // an entry (order-preserving key) in fixed point, 2^-32 units, rounded to nearest; exact
 // sums of these decide most MH tests (entries below 2^22 in magnitude, see FX_LIMIT)
@@ -369,6 +409,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         W.key[i] = S.cur_key[(size_t)c * n + i];
         W.nkey[i] = W.key[i];
         W.since[i] = F.t0;
+        W.brank[i] = S.best_rank[(size_t)c * n + i];
+        W.kst[i] = 0;
         // the cache index of node i's current best survivor
         uint32_t cj = 0;
         if (F.staged) {
@@ -396,6 +438,17 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         if (lane + 32 < n) W.pre[lane + 32] = (s1 | first_half) & ~b1;
     }
     double score = S.cur_score[c], best = S.best_score[c];
+    // Cached networks: Fcur = the exact fixed-point sum of the current entries; `dirty`: score
+    // not yet summed in FP64 for the current state; bestF / `bdirty` the same for the best
+    // state (bestF within guard_fx / 2 of best * 2^32 either way); `stale`: some kst[i] set
+    int64_t Fcur = 0, bestF = INT64_MIN / 4;
+    bool dirty = false, bdirty = false, stale = false;
+    if (F.staged) {
+        for (int i = lane; i < n; i += 32) Fcur += W.fx[i];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) Fcur += __shfl_xor_sync(0xffffffffu, Fcur, off);
+        if (isfinite(best)) bestF = __double2ll_rn(best * 4294967296.0);
+    }
     int64_t acc_count = 0, items = 0;
     // next recorded step and its index (recording: every record_every-th step from burn-in)
     int64_t rec_next = INT64_MAX, rec_idx = 0;
@@ -490,6 +543,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         items += b - a + 1;
         int acc = 1;
         double s2 = score;
+        bool lazy = false;
+        long long dfx = 0;
         if (moved) {
             __syncwarp();
             // MH test.  The exact test compares ln u with ln10 (s' - s), s' the FP64 sum over
@@ -503,7 +558,6 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             int exact = 0;
             acc = 0;
             if (F.staged) {
-                long long dfx = 0;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (node[h] >= 0) dfx += nfx[h] - W.fx[node[h]];
@@ -513,7 +567,14 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     const int q = it & 31;
                     exact = dfx < W.tlo[q] ? 0 : (dfx > W.thi[q] ? 1 : 2);     // equal in every lane
                 }
-                if (exact) {
+                // a move the fast test accepts needs no FP64 score now, unless per-step
+                // scores are traced
+                lazy = exact == 1 && t >= S.trace_cap;
+                if (exact && !lazy) {
+                    if (stale) {
+                        refresh_keys(S, W, n, lane);
+                        stale = false;
+                    }
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
                         if (node[h] >= 0) W.nkey[node[h]] = S.keys[(size_t)node[h] * S.Sp + nrank[h]];
@@ -536,20 +597,28 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 }
                 exact = __shfl_sync(0xffffffffu, exact, 0);
             }
-            if (lane == 0 && exact) {
-                // the proposal's keys: nkey holds the span's new keys and everyone else's
-                s2 = 0.0;
-                for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
-                if (exact == 2) {
-                    const double delta = __dsub_rn(s2, score);
-                    const double lu = log(W.ru[it & 31]);
-                    acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
-                } else {
-                    acc = 1;
+            if (exact && !lazy) {
+                if (dirty) {
+                    score = seq_score(W.key, n, lane);
+                    dirty = false;
                 }
+                if (lane == 0) {
+                    // the proposal's keys: nkey holds the span's new keys and everyone else's
+                    s2 = 0.0;
+                    for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+                    if (exact == 2) {
+                        const double delta = __dsub_rn(s2, score);
+                        const double lu = log(W.ru[it & 31]);
+                        acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+                    } else {
+                        acc = 1;
+                    }
+                }
+                acc = __shfl_sync(0xffffffffu, acc, 0);
+                s2 = __shfl_sync(0xffffffffu, s2, 0);
+            } else if (lazy) {
+                acc = 1;
             }
-            acc = __shfl_sync(0xffffffffu, acc, 0);
-            s2 = __shfl_sync(0xffffffffu, s2, 0);
         }
         // (not moved: no parent set changes, s' = s bit for bit and ln u < 0 accepts)
         if (!acc) {
@@ -567,7 +636,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                         credit_edges(S, c, nd, W.rank[nd], W.since[nd], t);
                         W.since[nd] = t;
                         W.rank[nd] = nrank[h];
-                        W.key[nd] = W.nkey[nd];
+                        if (lazy) W.kst[nd] = 1;
+                        else W.key[nd] = W.nkey[nd];
                         W.cj[nd] = wj[h];
                         if (F.staged) {
                             W.cmask[nd] = c_mask[wj[h]];
@@ -589,13 +659,56 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 W.ord[b] = (uint8_t)va;
             }
             __syncwarp();
-            score = s2;
             ++acc_count;
-            if (s2 > best) {
-                best = s2;
+            bool newbest;
+            if (!F.staged) {
+                score = s2;
+                newbest = s2 > best;
+            } else if (!moved) {
+                newbest = false;                        // s' = s <= best
+            } else {
+                Fcur += dfx;
+                if (lazy) {
+                    dirty = true;
+                    stale = true;
+                } else {
+                    score = s2;
+                }
+                const int64_t d = Fcur - bestF;
+                if (!dirty && !bdirty) {
+                    newbest = score > best;
+                } else if (d > F.guard_fx) {
+                    newbest = true;
+                } else if (d < -F.guard_fx) {
+                    newbest = false;
+                } else if (__all_sync(0xffffffffu, (lane >= n || W.rank[lane] == W.brank[lane]) &&
+                                                       (lane + 32 >= n || W.rank[lane + 32] == W.brank[lane + 32]))) {
+                    newbest = false;                    // the best state's parent sets: equal scores
+                } else {
+                    // too close to call in fixed point: both FP64 sums
+                    if (stale) {
+                        refresh_keys(S, W, n, lane);
+                        stale = false;
+                    }
+                    if (dirty) {
+                        score = seq_score(W.key, n, lane);
+                        dirty = false;
+                    }
+                    if (bdirty) {
+                        best = best_score_of(S, W, n, lane);
+                        bdirty = false;
+                    }
+                    newbest = score > best;
+                }
+            }
+            if (newbest) {
+                best = score;                           // (the FP64 value when !dirty)
+                bdirty = dirty;
+                bestF = Fcur;
                 for (int i = lane; i < n; i += 32) {
                     S.best_order[(size_t)c * n + i] = W.ord[i];
                     S.best_rank[(size_t)c * n + i] = W.rank[i];
+                    W.brank[i] = W.rank[i];
                 }
             }
         }
@@ -621,6 +734,10 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         __syncwarp();
     }
     const int64_t t_end = F.t0 + F.iters;
+    __syncwarp();
+    if (stale) refresh_keys(S, W, n, lane);
+    if (dirty) score = seq_score(W.key, n, lane);
+    if (bdirty) best = best_score_of(S, W, n, lane);
     for (int i = lane; i < n; i += 32) {
         credit_edges(S, c, i, W.rank[i], W.since[i], t_end);
         S.cur_order[(size_t)c * n + i] = W.ord[i];
@@ -934,6 +1051,7 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     F.staged = ch->t->alive_total <= SURV_CAP_MAX && ch->t->max_abs_survivor < FX_LIMIT ? 1 : 0;
     F.cap = F.staged ? (int)ch->t->alive_total : 0;
     F.margin_x = mh_margin(ch->S.n, ch->t->max_abs_survivor);
+    F.guard_fx = score_guard_fx(ch->S.n, ch->t->max_abs_survivor);
     size_t smem = 0;
     int rc = fused_smem_setup(F.cap, &smem);
     if (rc) return rc;
@@ -1506,6 +1624,7 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
             f.staged = t->alive_total <= cap && t->max_abs_survivor < FX_LIMIT ? 1 : 0;
             f.cap = cap;
             f.margin_x = mh_margin(t->n, t->max_abs_survivor);
+            f.guard_fx = score_guard_fx(t->n, t->max_abs_survivor);
             hit[(size_t)l * nf + i] = it;
         }
     }

@@ -45,6 +45,29 @@ def test_batch_equals_networks_alone(gpu):
             assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
 
 
+def test_batch_untraced_equals_full_scan_alone(gpu):
+    """The many-network launch without score traces (FP64 scores of fast-accepted moves
+    left for later) against each network stepped alone on its full table, per step."""
+    nets = _nets(5, 8)
+    tables = []
+    for data, ar, k in nets:
+        t = gpu.build_scores(data, ar, k)
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+        tables.append(t)
+    chains = [9, 32, 3, 20, 48]
+    seeds = [7 * i + 3 for i in range(len(tables))]
+    b = gpu.batch_create(tables, chains, seeds, burn_in=50)
+    for s in (300, 500):
+        b.step(s)
+    for i, t in enumerate(tables):
+        gpu.table_set_scan(t, gpu.SCAN_FULL)
+        alone = gpu.chains_create(t, chains[i], seeds[i], burn_in=50)
+        gpu.chains_step(alone, 800)
+        for what in ("orders", "scores", "best_scores", "best_orders", "best_ranks", "accepts", "edge_counts",
+                     "steps", "items"):
+            assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
+
+
 def test_batch_network_vs_oracle(gpu):
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     tab = oracle.build_table(data, arity, k, R=R)

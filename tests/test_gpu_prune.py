@@ -109,6 +109,30 @@ def test_fused_steps_equal_batched_steps(gpu):
     assert np.array_equal(np.isnan(ea), np.isnan(eb)) and np.allclose(ea[~np.isnan(ea)], eb[~np.isnan(eb)])
 
 
+@pytest.mark.parametrize("trace_cap", [0, 150])
+def test_fused_untraced_equals_batched_steps(gpu, trace_cap):
+    """Without per-step score traces the fused kernel leaves the FP64 score of moves its
+    fast test accepts for later, tracks the state by the exact fixed-point sum and decides
+    new bests in fixed point where that is provably the same decision; every output must
+    still equal the per-step path (which sums every accepted score in FP64), bit for bit.
+    Long enough that chains return to their best states and leave them again."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = gpu.build_scores(data, arity, k, R=R)
+    kw = dict(burn_in=100, record_every=7, record_cap=400, trace_cap=trace_cap)
+    a = gpu.chains_create(t, 64, 5151, **kw)
+    gpu.chains_step(a, 1500)                                 # batched, full scan
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    b = gpu.chains_create(t, 64, 5151, **kw)
+    for s in (500, 77, 923):                                 # fused, across chunk boundaries
+        gpu.chains_step(b, s)
+    outs = ["orders", "scores", "ranks", "best_orders", "best_scores", "best_ranks", "accepts", "edge_counts",
+            "record", "record_len", "steps", "items"]
+    if trace_cap:
+        outs += ["trace_score", "trace_accept"]
+    for what in outs:
+        assert np.array_equal(gpu.chains_read(a, what), gpu.chains_read(b, what)), what
+
+
 def test_switching_mode_recaptures_the_step(gpu):
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     t = gpu.build_scores(data, arity, k, R=R)
