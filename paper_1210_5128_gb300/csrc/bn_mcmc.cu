@@ -486,16 +486,19 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         const uint64_t bva = 1ull << va, bvb = 1ull << vb;
         // the span a..b of the proposed order: its nodes and their predecessor sets (the
         // current prefix with node va replaced by vb between a and b)
+        // lane l holds span positions a + l and, for spans longer than 32, a + l + 32
         int node[2] = {-1, -1};
         uint32_t nrank[2] = {0, 0};
         uint32_t wj[2] = {0, 0}, wj1[2] = {0, 0};
         uint64_t wnpc[2] = {0, 0};
         bool act[2] = {false, false};
         bool kept[2] = {false, false};
+        const int halves = b - a >= 32 ? 2 : 1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int p = lane + 32 * h;
-            if (p < n && p >= a && p <= b) {
+            if (h >= halves) break;
+            const int p = a + lane + 32 * h;
+            if (p <= b) {
                 const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
                 const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
                 wnpc[h] = ~compress_pred(excl, nd);
