@@ -84,14 +84,47 @@ __device__ __forceinline__ void credit_edges(const ChainState& S, int c, int v, 
     }
 }
 
-// The span's re-scoring walks, lane by lane: every lane has up to two nodes (h = 0, 1;
-// act[h]) and finds for each the first survivor j in [j[h], j1[h]) with (m[j] & npc[h]) == 0
-// (the last survivor, the empty set, always qualifies).  A lane walks its own nodes for
-// 16 survivors; nodes still open then are walked by the whole warp, 32 survivors a round.
-// On return j[h] holds the answer.  All 32 lanes must call it.
+// The whole warp walks one node's survivors [js, je), 32 a round; returns the first j with
+// (m[j] & np) == 0 (je - 1, the empty set, if none before it).
+__device__ __forceinline__ uint32_t warp_walk(const uint64_t* m, uint32_t js, uint32_t je, uint64_t np, int lane)
+{
+    for (uint32_t base = js; base < je; base += 32) {
+        const uint32_t idx = base + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, idx < je && (m[idx] & np) == 0ull);
+        if (b) return base + __ffs(b) - 1;
+    }
+    return je - 1;
+}
+
+// The span's re-scoring walks: every lane has up to two nodes (h = 0, 1; act[h]) and finds
+// for each the first survivor j in [j[h], j1[h]) with (m[j] & npc[h]) == 0 (the last
+// survivor, the empty set, always qualifies).  With few such nodes (the kept-set test of
+// the fused sampler leaves ~3 per step) the whole warp walks them one after another, 32
+// survivors a round; with many, every lane first walks its own nodes for 16 survivors and
+// the warp then walks those still open.  Either way j[h] holds the answer on return.  All
+// 32 lanes must call it.
+static constexpr int WARP_WALK_MAX = 8;
 __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], const uint32_t (&j1)[2],
                                           const uint64_t (&npc)[2], const bool (&act)[2], int lane)
 {
+    {
+        const unsigned p0 = __ballot_sync(0xffffffffu, act[0]), p1 = __ballot_sync(0xffffffffu, act[1]);
+        if (__popc(p0) + __popc(p1) <= WARP_WALK_MAX) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned pend = h ? p1 : p0;
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const uint32_t js = __shfl_sync(0xffffffffu, j[h], src), je = __shfl_sync(0xffffffffu, j1[h], src);
+                    const uint64_t np = __shfl_sync(0xffffffffu, npc[h], src);
+                    const uint32_t hit = warp_walk(m, js, je, np, lane);
+                    if (lane == src) j[h] = hit;
+                }
+            }
+            return;
+        }
+    }
     bool open[2] = {false, false};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -122,15 +155,7 @@ __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], c
             pend &= pend - 1;
             const uint32_t js = __shfl_sync(0xffffffffu, j[h], src), je = __shfl_sync(0xffffffffu, j1[h], src);
             const uint64_t np = __shfl_sync(0xffffffffu, npc[h], src);
-            uint32_t hit = je - 1;
-            for (uint32_t base = js; base < je; base += 32) {
-                const uint32_t idx = base + lane;
-                const unsigned b = __ballot_sync(0xffffffffu, idx < je && (m[idx] & np) == 0ull);
-                if (b) {
-                    hit = base + __ffs(b) - 1;
-                    break;
-                }
-            }
+            const uint32_t hit = warp_walk(m, js, je, np, lane);
             if (lane == src) j[h] = hit;
         }
     }
