@@ -98,18 +98,20 @@ __device__ __forceinline__ uint32_t warp_walk(const uint64_t* m, uint32_t js, ui
 
 // The span's re-scoring walks: every lane has up to two nodes (h = 0, 1; act[h]) and finds
 // for each the first survivor j in [j[h], j1[h]) with (m[j] & npc[h]) == 0 (the last
-// survivor, the empty set, always qualifies).  With few such nodes (the kept-set test of
-// the fused sampler leaves ~3 per step) the whole warp walks them one after another, 32
-// survivors a round; with many, every lane first walks its own nodes for 16 survivors and
-// the warp then walks those still open.  Either way j[h] holds the answer on return.  All
-// 32 lanes must call it.
-static constexpr int WARP_WALK_MAX = 8;
+// survivor, the empty set, always qualifies); on return j[h] holds the answer.  All 32
+// lanes must call it.  With at most `warp_max` such nodes the whole warp walks them one
+// after another, 32 survivors a round (the fused sampler on a cached network, whose
+// kept-set test leaves ~3 nodes per step: measured on GB300 at n = 60, 1.66 us per step
+// with warp walks always against 1.70 us with lane walks above 8 nodes and 1.73 us above
+// 3); with more, every lane first walks its own nodes for 16 survivors and the warp then
+// walks those still open (every span node re-scored: uncached networks, learned steps).
 __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], const uint32_t (&j1)[2],
-                                          const uint64_t (&npc)[2], const bool (&act)[2], int lane)
+                                          const uint64_t (&npc)[2], const bool (&act)[2], int lane,
+                                          int warp_max)
 {
     {
         const unsigned p0 = __ballot_sync(0xffffffffu, act[0]), p1 = __ballot_sync(0xffffffffu, act[1]);
-        if (__popc(p0) + __popc(p1) <= WARP_WALK_MAX) {
+        if (__popc(p0) + __popc(p1) <= warp_max) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 unsigned pend = h ? p1 : p0;

@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
                     act[h] = true;
                 }
             }
-            span_walk(smask, wj, wj1, wnpc, act, lane);
+            span_walk(smask, wj, wj1, wnpc, act, lane, 8);
             double dpart = 0.0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {

@@ -393,6 +393,7 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
     }
 }
 
+template <bool STAGED>
 __device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
                                                  FusedSmem& W, const uint8_t* cache)
 {
@@ -413,7 +414,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         W.kst[i] = 0;
         // the cache index of node i's current best survivor
         uint32_t cj = 0;
-        if (F.staged) {
+        if (STAGED) {
             for (cj = c_off[i]; cj + 1 < c_off[i + 1] && c_rank[cj] != W.rank[i]; ++cj) {}
             W.cmask[i] = c_mask[cj];
             W.corb[i] = c_orb[cj];
@@ -443,7 +444,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     // state (bestF within guard_fx / 2 of best * 2^32 either way); `stale`: some kst[i] set
     int64_t Fcur = 0, bestF = INT64_MIN / 4;
     bool dirty = false, bdirty = false, stale = false;
-    if (F.staged) {
+    if (STAGED) {
         for (int i = lane; i < n; i += 32) Fcur += W.fx[i];
 #pragma unroll
         for (int off = 16; off; off >>= 1) Fcur += __shfl_xor_sync(0xffffffffu, Fcur, off);
@@ -503,7 +504,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                 const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
                 wnpc[h] = ~compress_pred(excl, nd);
                 node[h] = nd;
-                if (F.staged) {
+                if (STAGED) {
                     // The node's best set so far is the first survivor consistent with its
                     // old predecessors.  A survivor before it can only become consistent by
                     // containing a gained predecessor; if none does, the answer is that set
@@ -525,14 +526,14 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             }
         }
         // survivors of each node in score order: the first consistent one wins
-        span_walk(F.staged ? c_mask : F.amask, wj, wj1, wnpc, act, lane);
+        span_walk(STAGED ? c_mask : F.amask, wj, wj1, wnpc, act, lane, STAGED ? 64 : 8);
         bool moved = false;
         int64_t nfx[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (!act[h] && !kept[h]) continue;
             const int nd = node[h];
-            if (F.staged) {
+            if (STAGED) {
                 // the new key is fetched only if the exact test needs it
                 nrank[h] = c_rank[wj[h]];
                 nfx[h] = c_fx[wj[h]];
@@ -560,7 +561,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             // fetches the span's new FP64 entries.
             int exact = 0;
             acc = 0;
-            if (F.staged) {
+            if (STAGED) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (node[h] >= 0) dfx += nfx[h] - W.fx[node[h]];
@@ -642,7 +643,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                         if (lazy) W.kst[nd] = 1;
                         else W.key[nd] = W.nkey[nd];
                         W.cj[nd] = wj[h];
-                        if (F.staged) {
+                        if (STAGED) {
                             W.cmask[nd] = c_mask[wj[h]];
                             W.corb[nd] = c_orb[wj[h]];
                             W.fx[nd] = nfx[h];
@@ -664,7 +665,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             __syncwarp();
             ++acc_count;
             bool newbest;
-            if (!F.staged) {
+            if (!STAGED) {
                 score = s2;
                 newbest = s2 > best;
             } else if (!moved) {
@@ -757,18 +758,20 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
 
 __host__ __device__ constexpr size_t surv_cache_stride(int cap) { return (surv_cache_bytes(cap) + 15) / 16 * 16; }
 
+// STAGED: the network's survivors sit in the block's shared-memory cache (F.staged)
+template <bool STAGED>
 __global__ void __launch_bounds__(32 * FUSED_WARPS) k_chain_fused(ChainState S, FusedArgs F)
 {
     __shared__ FusedSmem sm[FUSED_WARPS];
     extern __shared__ __align__(16) uint8_t fcache[];     // one survivor cache per block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * FUSED_WARPS + warp;
-    if (F.staged) {
+    if (STAGED) {
         fill_surv_cache(S, F, fcache, threadIdx.x, blockDim.x);
         __syncthreads();
     }
     if (c >= S.C) return;
-    chain_fused_body(S, F, c, lane, sm[warp], fcache);
+    chain_fused_body<STAGED>(S, F, c, lane, sm[warp], fcache);
 }
 
 // many networks' chains in one launch: block g belongs to the network i with
@@ -797,7 +800,8 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
     }
     const int64_t c = (g - cta_base[lo]) * BATCH_WARPS + warp;
     if (c >= S.C) return;
-    chain_fused_body(S, F, (int)c, lane, sm[warp], fcache);
+    if (F.staged) chain_fused_body<true>(S, F, (int)c, lane, sm[warp], fcache);
+    else chain_fused_body<false>(S, F, (int)c, lane, sm[warp], fcache);
 }
 
 static int fused_smem_setup(int cap, size_t* smem)
@@ -806,7 +810,8 @@ static int fused_smem_setup(int cap, size_t* smem)
     const int d = device_id();
     const size_t mx = surv_cache_stride(SURV_CAP_MAX);
     if (d < 64 && !done[d]) {
-        BN_CUDA(cudaFuncSetAttribute(k_chain_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        BN_CUDA(cudaFuncSetAttribute(k_chain_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        BN_CUDA(cudaFuncSetAttribute(k_chain_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         done[d] = true;
     }
@@ -1059,7 +1064,8 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     int rc = fused_smem_setup(F.cap, &smem);
     if (rc) return rc;
     if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
-    k_chain_fused<<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
+    if (F.staged) k_chain_fused<true><<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
+    else k_chain_fused<false><<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
     BN_LAUNCH_CHECK("k_chain_fused");
     if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_step_advance<<<1, 1, 0, s>>>(ch->S, iters);
