@@ -422,7 +422,7 @@ def main():
         launches = bn.kernel_launches() - l0
         barrier()
         clocks = clk.stop()
-        # the fused sampler kernel, launch by launch (256 iterations per launch)
+        # the fused sampler kernel, launch by launch (up to 1024 iterations per launch)
         fused_ms, fused_l = bn.chains_step_profiled(chains, max(ips, 256) * 4, stream=stream.cuda_stream)
         chains.free()
 
@@ -486,7 +486,7 @@ def main():
                  "n_range": [min(d_.shape[1] for d_, *_ in nets), max(d_.shape[1] for d_, *_ in nets)],
                  "table_entries": int(b_entries), "table_build_s": b_build,
                  "table_entries_per_s": b_entries / b_build,
-                 "note": "uniform-swap chains of every network in one fused launch per 256 steps "
+                 "note": "uniform-swap chains of every network in one fused launch per 1024 steps "
                          "(bn_batch_step); the learned proposal runs per network (bn_chains_set_proposal)"}
         bat.free()
         for tb in tabs:
@@ -548,7 +548,7 @@ def main():
                              "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_leg[0]["frac"], "traffic": None, "peak_source": peak_src,
                              "bytes_algorithmic": hbm_bytes, "by_orders": hbm_leg},
-            "pruned_step": {"kernel": "k_chain_fused (256 MH iterations per launch, one warp per chain)",
+            "pruned_step": {"kernel": "k_chain_fused (up to 1024 MH iterations per launch, one warp per chain)",
                             "avg_ms_per_launch": avg_fused, "launches": fused_l,
                             "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
                             "survivors_per_node_mean": float(survivors.mean()),

@@ -274,7 +274,7 @@ int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
 /* Batches of networks of uneven size (the paper samples one network at a time): count
  * networks, each with its own table and chain parameters.  bn_batch_step advances every
  * network by `steps` MH steps; the networks whose chains use the uniform proposal on a
- * pruned table (BN_SCAN_PRUNED) advance together in one fused launch per 256 steps (one
+ * pruned table (BN_SCAN_PRUNED) advance together in one fused launch per 1024 steps (one
  * warp per chain of every network), the others through their own per-network steps.
  * Results equal stepping each network's chains alone.  bn_batch_chains gives network
  * i's chains (for bn_chains_read / bn_chains_set_proposal); they are freed with the

@@ -1038,7 +1038,7 @@ __global__ void k_pick_best(const double* __restrict__ best_score, const uint8_t
 
 using namespace bn;
 
-static constexpr int FUSED_ITERS = 256;     // MH steps per fused launch
+static constexpr int FUSED_ITERS = 1024;    // MH steps per fused launch
 
 static bool fused_path(const bn_chains* ch)
 {
