@@ -277,9 +277,11 @@ struct FusedArgs {
                          // this (2^-32 units) compare the same way as their FP64 sums
 };
 
-// shared-memory cache of a network's survivors: candidate mask, the entry in 64-bit fixed
-// point (2^-32 units), the OR of the masks of the node's survivors before it, and rank of
-// every survivor (score order), and the node offsets
+// shared-memory cache of a network's survivors: parent mask in node space (bit v = node v;
+// the table's candidate-space masks with a 0 inserted at the child's own bit, so the span's
+// predecessor masks test against it directly), the entry in 64-bit fixed point (2^-32
+// units), the OR of the masks of the node's survivors before it, and rank of every
+// survivor (score order), and the node offsets
 __host__ __device__ constexpr size_t surv_cache_bytes(int cap)
 {
     return (size_t)cap * (8 + 8 + 8 + 4) + 4 * (MAXN + 1);
@@ -300,7 +302,7 @@ struct FusedSmem {
     int64_t since[MAXN];
     uint64_t pre[MAXN];        // nodes at positions < p of the current order
     uint32_t cj[MAXN];         // cache index of each node's current best survivor,
-    uint64_t cmask[MAXN];      //   its candidate mask
+    uint64_t cmask[MAXN];      //   its parent mask (node space, cached networks)
     uint64_t corb[MAXN];       //   and the OR of the masks of the node's survivors before it
     int64_t fx[MAXN];          // each node's current entry in fixed point (cached networks)
     uint8_t ra[32], rb[32];    // the next 32 steps: the swapped positions a < b,
@@ -376,7 +378,9 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
             else hi = mid;
         }
         const uint32_t r = S.srank[(size_t)lo * S.Sp + F.aspos[o0 + j]];
-        c_mask[j] = F.amask[o0 + j];
+        const uint64_t cm = F.amask[o0 + j];
+        const uint64_t below = lo ? (~0ull >> (64 - lo)) : 0ull;
+        c_mask[j] = (cm & below) | ((cm & ~below) << 1);
         c_rank[j] = r;
         c_fx[j] = entry_fx(S.keys[(size_t)lo * S.Sp + r]);
     }
@@ -502,7 +506,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             if (p <= b) {
                 const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
                 const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
-                wnpc[h] = ~compress_pred(excl, nd);
+                // cached networks test node-space masks; the table's are in candidate space
+                wnpc[h] = STAGED ? ~excl : ~compress_pred(excl, nd);
                 node[h] = nd;
                 if (STAGED) {
                     // The node's best set so far is the first survivor consistent with its
@@ -510,7 +515,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     // containing a gained predecessor; if none does, the answer is that set
                     // again (still consistent) or lies after it.
                     const uint64_t old_pred = (p == a) ? W.pre[b] : (p == b) ? W.pre[a] : W.pre[p];
-                    const uint64_t gained = compress_pred(excl & ~old_pred, nd);
+                    const uint64_t gained = excl & ~old_pred;
                     const uint32_t cj = W.cj[nd];
                     const bool none_before = (W.corb[nd] & gained) == 0ull;
                     const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
