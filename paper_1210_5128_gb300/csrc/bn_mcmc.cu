@@ -570,8 +570,14 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (node[h] >= 0) dfx += nfx[h] - W.fx[node[h]];
-#pragma unroll
-                for (int off = 16; off; off >>= 1) dfx += __shfl_xor_sync(0xffffffffu, dfx, off);
+                // warp sum in three 21-bit limbs (|lane value| < 2^56, so no limb sum
+                // overflows 32 bits), one reduction instruction each
+                {
+                    const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(dfx & 0x1fffff));
+                    const unsigned mid = __reduce_add_sync(0xffffffffu, (unsigned)((dfx >> 21) & 0x1fffff));
+                    const int hi = __reduce_add_sync(0xffffffffu, (int)(dfx >> 42));
+                    dfx = (long long)hi * (1ll << 42) + (long long)mid * (1ll << 21) + (long long)lo;
+                }
                 {
                     const int q = it & 31;
                     exact = dfx < W.tlo[q] ? 0 : (dfx > W.thi[q] ? 1 : 2);     // equal in every lane
