@@ -553,6 +553,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         int acc = 1;
         double s2 = score;
         bool lazy = false;
+        int exact = 0;
         long long dfx = 0;
         if (moved) {
             __syncwarp();
@@ -564,7 +565,6 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             // are farther apart than both errors the decision is the exact one.  Close calls
             // and accepted moves (whose new score the state keeps) take the exact path, which
             // fetches the span's new FP64 entries.
-            int exact = 0;
             acc = 0;
             if (STAGED) {
 #pragma unroll
@@ -636,8 +636,9 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             }
         }
         // (not moved: no parent set changes, s' = s bit for bit and ln u < 0 accepts)
-        if (!acc) {
-            // the rejected proposal's keys: nkey equals key again outside any span
+        if (!acc && (!STAGED || exact)) {
+            // the rejected proposal's keys: nkey equals key again outside any span (cached
+            // networks change nkey only on the exact path)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 if (node[h] >= 0) W.nkey[node[h]] = W.key[node[h]];
@@ -662,13 +663,14 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     }
                 }
             }
-            // prefixes of positions a+1..b now hold vb instead of va
+            // prefixes of positions a+1..b now hold vb instead of va (lane l: a + 1 + l and,
+            // for b - a > 32, a + 33 + l)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int p = lane + 32 * h;
-                if (p < n && p > a && p <= b) W.pre[p] = (W.pre[p] & ~bva) | bvb;
+                if (h == 1 && b - a <= 32) break;
+                const int p = a + 1 + lane + 32 * h;
+                if (p <= b) W.pre[p] = (W.pre[p] & ~bva) | bvb;
             }
-            __syncwarp();
             if (lane == 0) {
                 W.ord[a] = (uint8_t)vb;
                 W.ord[b] = (uint8_t)va;
