@@ -23,6 +23,20 @@
 
 namespace bn {
 
+// best = min(best, sp) if (m & npc) == 0, npc = (nhi:nlo): the two halves ANDed and ORed
+// by two three-input logic ops, the zero test on that word, a predicated min
+__device__ __forceinline__ void test_min(uint32_t& best, uint32_t mlo, uint32_t mhi, uint32_t nlo, uint32_t nhi,
+                                         uint32_t sp)
+{
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t, u;\n\t"
+        "lop3.b32 t, %1, %3, 0, 0xC0;\n\t"
+        "lop3.b32 u, %2, %4, t, 0xEA;\n\t"
+        "setp.eq.u32 p, u, 0;\n\t"
+        "@p min.u32 %0, %0, %5;\n\t}"
+        : "+r"(best)
+        : "r"(mlo), "r"(mhi), "r"(nlo), "r"(nhi), "r"(sp));
+}
+
 static constexpr int SCAN_THREADS = 256;
 static constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 // stage size (entries) and pipeline depth; 48 KB of shared memory for the 1024 and 512
@@ -173,6 +187,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     const int sub = lane % LPI;
     const bool active = warp_on && item < cnt;
     const uint64_t npc = active ? ~A.list_pc[(size_t)node * A.cap + item] : ~0ull;
+    const uint32_t nlo = (uint32_t)npc, nhi = (uint32_t)(npc >> 32);
     const int nsub = (int)((e1 - e0 + SCAN_SUB - 1) / SCAN_SUB);
 
     uint64_t pol_stream = 0, pol_keep = 0;
@@ -226,9 +241,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
 #pragma unroll 4
             for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
                 const uint2 pp = P[j];
-                const ulonglong2 mm = M[j];
-                if ((mm.x & npc) == 0ull) b0 = min(b0, pp.x);
-                if ((mm.y & npc) == 0ull) b1 = min(b1, pp.y);
+                const uint4 mm = ((const uint4*)M)[j];
+                test_min(b0, mm.x, mm.y, nlo, nhi, pp.x);
+                test_min(b1, mm.z, mm.w, nlo, nhi, pp.y);
             }
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
