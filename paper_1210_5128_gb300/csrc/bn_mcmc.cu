@@ -498,6 +498,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
         uint64_t wnpc[2] = {0, 0};
         bool act[2] = {false, false};
         bool kept[2] = {false, false};
+        uint32_t cjv[2] = {0, 0};        // cached networks: the node's current survivor index
         const int halves = b - a >= 32 ? 2 : 1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -517,6 +518,7 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     const uint64_t old_pred = (p == a) ? W.pre[b] : (p == b) ? W.pre[a] : W.pre[p];
                     const uint64_t gained = excl & ~old_pred;
                     const uint32_t cj = W.cj[nd];
+                    cjv[h] = cj;
                     const bool none_before = (W.corb[nd] & gained) == 0ull;
                     const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
                     wj[h] = none_before ? (stays ? cj : cj + 1) : c_off[nd];
@@ -539,14 +541,16 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
             if (!act[h] && !kept[h]) continue;
             const int nd = node[h];
             if (STAGED) {
-                // the new key is fetched only if the exact test needs it
+                // the new key is fetched only if the exact test needs it; survivor indices
+                // are unique per node, so the set changed iff the index did
                 nrank[h] = c_rank[wj[h]];
                 nfx[h] = c_fx[wj[h]];
+                moved |= wj[h] != cjv[h];
             } else {
                 nrank[h] = S.srank[(size_t)nd * S.Sp + F.aspos[wj[h]]];
                 W.nkey[nd] = S.keys[(size_t)nd * S.Sp + nrank[h]];
+                moved |= nrank[h] != W.rank[nd];
             }
-            moved |= nrank[h] != W.rank[nd];
         }
         moved = __any_sync(0xffffffffu, moved);
         items += b - a + 1;
