@@ -525,7 +525,11 @@ def main():
                                     "launches": scan_l_full,
                                     "hbm_bytes_algorithmic": 12 * n * S,
                                     "hbm_frac_of_measured": 12 * n * S / (avg_full / 1000.0) / 1e9 / hbm_peak},
-                     "share_of_step": avg_full / (ms_full / args.steps)}
+                     "share_of_step": avg_full / (ms_full / args.steps),
+                     "note": "the paper's scan (a6) over the full table for a step of all chains' orders, timed "
+                             "in this run (full_scan); the headline step runs the pruned fused sampler "
+                             "k_chain_fused instead, which is latency-bound (one warp per chain, under two "
+                             "warps per SM; see pruned_step and profiles/k_chain_fused_n60_256chains.md)"}
         avg_fused = fused_ms / max(fused_l, 1)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
