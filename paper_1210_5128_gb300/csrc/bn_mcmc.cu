@@ -12,6 +12,14 @@
 //   k_scan     the order-score scan of those (node, chain) items
 //   k_accept   chunk combine, FP64 order score (ascending node id), MH test, best
 //              graph, edge counts, trace/ESS records; the last block advances the step
+// On a pruned table with the uniform proposal one kernel does all of it instead:
+//   k_chain_fused  one warp per chain, up to 1024 steps per launch, the network's
+//              survivors in shared memory; per step only the span's nodes that cannot
+//              keep their parent sets are re-scored, the MH test is decided on exact
+//              fixed-point changes against thresholds prepared with the Philox draws,
+//              and FP64 order scores are formed only where a decision or an output needs
+//              them (every decision equal to the per-step path's)
+//   k_batch_fused  the same for many networks' chains in one launch
 #include <algorithm>
 #include <cmath>
 #include <cstring>
