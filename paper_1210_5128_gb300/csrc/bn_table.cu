@@ -289,12 +289,17 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build(BuildArgs A)
             if (ri == 2) acc = score_cells<2>(hist, q, Lx, Lc, lane);
             else if (ri == 3) acc = score_cells<3>(hist, q, Lx, Lc, lane);
             else acc = score_cells<4>(hist, q, Lx, Lc, lane);
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
-                lo = __shfl_xor_sync(0xffffffffu, lo, off);
-                hi = __shfl_xor_sync(0xffffffffu, hi, off);
-                acc += ((fx128)hi << 64) | (fx128)lo;
+            // warp sum, exact mod 2^128: five limbs (26, 26, 26, 26, 24 bits) of every lane's
+            // value summed by one 32-bit reduction instruction each (32 lanes x 2^26 < 2^32)
+            {
+                const uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
+                constexpr uint64_t M26 = (1ull << 26) - 1;
+                const uint32_t s0 = __reduce_add_sync(0xffffffffu, (uint32_t)(lo & M26));
+                const uint32_t s1 = __reduce_add_sync(0xffffffffu, (uint32_t)((lo >> 26) & M26));
+                const uint32_t s2 = __reduce_add_sync(0xffffffffu, (uint32_t)(((lo >> 52) | (hi << 12)) & M26));
+                const uint32_t s3 = __reduce_add_sync(0xffffffffu, (uint32_t)((hi >> 14) & M26));
+                const uint32_t s4 = __reduce_add_sync(0xffffffffu, (uint32_t)(hi >> 40));
+                acc = (fx128)s0 + ((fx128)s1 << 26) + ((fx128)s2 << 52) + ((fx128)s3 << 78) + ((fx128)s4 << 104);
             }
             // every lane holds the sum; lane (rho - r0) % 32 finishes this entry, 32 entries
             // at a time (the FP64 tail runs on all lanes instead of on one)
