@@ -223,14 +223,19 @@ int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, const uint8_t* 
  * others keep their predecessor sets, so their best parent sets are unchanged),
  * applies the MH test, updates the best graph (strictly better replaces; candidates are
  * the initial and the accepted orders) and, after burn-in, the edge counts of the
- * current state's greedy DAG.  Steps are replayed from a captured CUDA graph.
+ * current state's greedy DAG.  Steps are replayed from a captured CUDA graph; on a
+ * pruned table (BN_SCAN_PRUNED) with the uniform proposal one fused kernel advances every
+ * chain up to 1024 steps per launch instead, with identical results (it forms a step's
+ * FP64 order score only where the MH test, a trace, the best state or the chain's saved
+ * state needs it).  Synchronous with `stream`.
  * Errors: BN_ETIMEOUT, BN_ECUDA. */
 int bn_chains_step(bn_chains* c, int64_t steps, void* stream);
 
 /* bn_chains_step without the graph: the step's kernels are launched one by one on
- * `stream` and every scan launch is bracketed by a pair of CUDA events; *scan_ms
- * receives the summed device time of those launches and *scan_launches their number
- * (either may be NULL).  Results are identical to bn_chains_step. */
+ * `stream` and every scan launch (on the fused path: every fused launch) is bracketed by
+ * a pair of CUDA events; *scan_ms receives the summed device time of those launches and
+ * *scan_launches their number (either may be NULL).  Results are identical to
+ * bn_chains_step. */
 int bn_chains_step_profiled(bn_chains* c, int64_t steps, void* stream, double* scan_ms,
                             int64_t* scan_launches);
 
