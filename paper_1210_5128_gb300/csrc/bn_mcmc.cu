@@ -279,7 +279,9 @@ struct FusedArgs {
     int64_t t0;          // first step of this launch
     int iters;
     int staged;          // 1: the network's survivors fit the warp's shared-memory cache
-    int cap;             // survivors per warp cache (shared-memory layout of the launch)
+    int cap;             // survivors per warp cache (shared-memory layout of the launch;
+                         // the table's survivor count for a global-memory cache)
+    const uint8_t* gcache;   // not staged: the same cache in global memory, or null
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
     int64_t guard_fx;    // two order scores whose exact fixed-point sums differ by more than
                          // this (2^-32 units) compare the same way as their FP64 sums
@@ -402,6 +404,48 @@ __device__ __forceinline__ void fill_surv_cache(const ChainState& S, const Fused
             c_orb[j] = acc;
             acc |= c_mask[j];
         }
+    }
+}
+
+// The survivors in the cache layout above, in global memory (one thread per survivor; the
+// prefix ORs one thread per node, in a second launch)
+__global__ void k_gcache_fill(const int64_t* __restrict__ keys, const uint32_t* __restrict__ srank, int64_t Sp,
+                              int n, const uint64_t* __restrict__ amask, const uint32_t* __restrict__ aspos,
+                              const uint32_t* __restrict__ aoff, uint32_t total, int cap, uint8_t* __restrict__ cache)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t* c_mask = (uint64_t*)cache;
+    int64_t* c_fx = (int64_t*)(cache + 8 * (size_t)cap);
+    uint32_t* c_rank = (uint32_t*)(cache + 24 * (size_t)cap);
+    uint32_t* c_off = (uint32_t*)(cache + 28 * (size_t)cap);
+    if (j < total) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (aoff[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t r = srank[(size_t)lo * Sp + aspos[j]];
+        const uint64_t cm = amask[j];
+        const uint64_t below = lo ? (~0ull >> (64 - lo)) : 0ull;
+        c_mask[j] = (cm & below) | ((cm & ~below) << 1);
+        c_rank[j] = r;
+        c_fx[j] = entry_fx(keys[(size_t)lo * Sp + r]);
+    }
+    if (j <= (uint32_t)n) c_off[j] = j < (uint32_t)n ? aoff[j] : total;
+}
+
+__global__ void k_gcache_orb(int n, int cap, uint8_t* __restrict__ cache)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint64_t* c_mask = (const uint64_t*)cache;
+    uint64_t* c_orb = (uint64_t*)(cache + 16 * (size_t)cap);
+    const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)cap);
+    uint64_t acc = 0ull;
+    for (uint32_t j = c_off[v]; j < c_off[v + 1]; ++j) {
+        c_orb[j] = acc;
+        acc |= c_mask[j];
     }
 }
 
@@ -783,20 +827,21 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
 
 __host__ __device__ constexpr size_t surv_cache_stride(int cap) { return (surv_cache_bytes(cap) + 15) / 16 * 16; }
 
-// STAGED: the network's survivors sit in the block's shared-memory cache (F.staged)
-template <bool STAGED>
+// MODE 1: the network's survivors in the block's shared-memory cache (F.staged); 2: the
+// same layout in global memory (F.gcache); 0: the table's survivor arrays
+template <int MODE>
 __global__ void __launch_bounds__(32 * FUSED_WARPS) k_chain_fused(ChainState S, FusedArgs F)
 {
     __shared__ FusedSmem sm[FUSED_WARPS];
     extern __shared__ __align__(16) uint8_t fcache[];     // one survivor cache per block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * FUSED_WARPS + warp;
-    if (STAGED) {
+    if (MODE == 1) {
         fill_surv_cache(S, F, fcache, threadIdx.x, blockDim.x);
         __syncthreads();
     }
     if (c >= S.C) return;
-    chain_fused_body<STAGED>(S, F, c, lane, sm[warp], fcache);
+    chain_fused_body<MODE != 0>(S, F, c, lane, sm[warp], MODE == 2 ? F.gcache : fcache);
 }
 
 // many networks' chains in one launch: block g belongs to the network i with
@@ -826,7 +871,28 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
     const int64_t c = (g - cta_base[lo]) * BATCH_WARPS + warp;
     if (c >= S.C) return;
     if (F.staged) chain_fused_body<true>(S, F, (int)c, lane, sm[warp], fcache);
+    else if (F.gcache) chain_fused_body<true>(S, F, (int)c, lane, sm[warp], F.gcache);
     else chain_fused_body<false>(S, F, (int)c, lane, sm[warp], fcache);
+}
+
+int build_survivor_cache(bn_table* t, cudaStream_t s)
+{
+    if (t->gcache || !t->amask || t->alive_total <= SURV_CAP_MAX || !(t->max_abs_survivor < FX_LIMIT)) return BN_OK;
+    const int cap = (int)t->alive_total;
+    uint8_t* g = nullptr;
+    cudaError_t e = cudaMalloc((void**)&g, surv_cache_stride(cap));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BN_OK;                       // no cache: the uncached walk still works
+    }
+    const uint32_t total = (uint32_t)cap;
+    const unsigned blocks = (unsigned)((std::max<uint32_t>(total, (uint32_t)t->n + 1) + 255) / 256);
+    k_gcache_fill<<<blocks, 256, 0, s>>>(t->keys, t->srank, t->Sp, t->n, t->amask, t->aspos, t->aoff, total, cap, g);
+    BN_LAUNCH_CHECK("k_gcache_fill");
+    k_gcache_orb<<<(t->n + 63) / 64, 64, 0, s>>>(t->n, cap, g);
+    BN_LAUNCH_CHECK("k_gcache_orb");
+    t->gcache = g;
+    return BN_OK;
 }
 
 static int fused_smem_setup(int cap, size_t* smem)
@@ -835,8 +901,7 @@ static int fused_smem_setup(int cap, size_t* smem)
     const int d = device_id();
     const size_t mx = surv_cache_stride(SURV_CAP_MAX);
     if (d < 64 && !done[d]) {
-        BN_CUDA(cudaFuncSetAttribute(k_chain_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-        BN_CUDA(cudaFuncSetAttribute(k_chain_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        BN_CUDA(cudaFuncSetAttribute(k_chain_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         done[d] = true;
     }
@@ -1082,15 +1147,19 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     F.t0 = t0;
     F.iters = iters;
     F.staged = ch->t->alive_total <= SURV_CAP_MAX && ch->t->max_abs_survivor < FX_LIMIT ? 1 : 0;
-    F.cap = F.staged ? (int)ch->t->alive_total : 0;
+    F.gcache = F.staged ? nullptr : ch->t->gcache;
+    F.cap = (F.staged || F.gcache) ? (int)ch->t->alive_total : 0;
     F.margin_x = mh_margin(ch->S.n, ch->t->max_abs_survivor);
     F.guard_fx = score_guard_fx(ch->S.n, ch->t->max_abs_survivor);
     size_t smem = 0;
-    int rc = fused_smem_setup(F.cap, &smem);
+    int rc = fused_smem_setup(F.staged ? F.cap : 0, &smem);
     if (rc) return rc;
+    if (!F.staged) smem = 0;
+    const unsigned grid = (unsigned)((ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS);
     if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
-    if (F.staged) k_chain_fused<true><<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
-    else k_chain_fused<false><<<(ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
+    if (F.staged) k_chain_fused<1><<<grid, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
+    else if (F.gcache) k_chain_fused<2><<<grid, 32 * FUSED_WARPS, 0, s>>>(ch->S, F);
+    else k_chain_fused<0><<<grid, 32 * FUSED_WARPS, 0, s>>>(ch->S, F);
     BN_LAUNCH_CHECK("k_chain_fused");
     if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_step_advance<<<1, 1, 0, s>>>(ch->S, iters);
@@ -1656,7 +1725,8 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
             f.t0 = fused[i]->steps + done;
             f.iters = it;
             f.staged = t->alive_total <= cap && t->max_abs_survivor < FX_LIMIT ? 1 : 0;
-            f.cap = cap;
+            f.gcache = f.staged ? nullptr : t->gcache;
+            f.cap = f.gcache ? (int)t->alive_total : cap;
             f.margin_x = mh_margin(t->n, t->max_abs_survivor);
             f.guard_fx = score_guard_fx(t->n, t->max_abs_survivor);
             hit[(size_t)l * nf + i] = it;

@@ -315,7 +315,7 @@ int prune_table(bn_table* t, cudaStream_t s)
     memcpy(&mx_abs, &hmx, 8);
     t->max_abs_survivor = mx_abs;
     (void)offs;
-    return BN_OK;
+    return build_survivor_cache(t, s);
 }
 
 }  // namespace bn

@@ -729,5 +729,6 @@ extern "C" void bn_table_free(bn_table* t)
     cudaFree(t->srank);
     cudaFree(t->spos_t);
     cudaFree(t->alive_block);
+    cudaFree(t->gcache);
     delete t;
 }
