@@ -320,6 +320,8 @@ struct FusedSmem {
     int64_t tlo[32], thi[32];  //   and the fast test's thresholds (ln u -/+ its margin) in
                                //   the fixed-point units of the change, 2^-32 of a score
     uint32_t brank[MAXN];      // ranks of the best state so far
+    uint32_t coff[MAXN + 1];   // cached networks: the nodes' first survivor indices (a copy
+                               // of the cache's, which may sit in global memory)
     uint8_t kst[MAXN];         // 1: key[i] (and nkey[i]) not yet read for the node's rank
 };
 
@@ -460,6 +462,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
     const uint64_t* c_orb = (const uint64_t*)(cache + 16 * (size_t)F.cap);
     const uint32_t* c_rank = (const uint32_t*)(cache + 24 * (size_t)F.cap);
     const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)F.cap);
+    if (STAGED)
+        for (int i = lane; i <= n; i += 32) W.coff[i] = c_off[i];
     for (int i = lane; i < n; i += 32) {
         W.ord[i] = S.cur_order[(size_t)c * n + i];
         W.rank[i] = S.cur_rank[(size_t)c * n + i];
@@ -573,8 +577,8 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     cjv[h] = cj;
                     const bool none_before = (W.corb[nd] & gained) == 0ull;
                     const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
-                    wj[h] = none_before ? (stays ? cj : cj + 1) : c_off[nd];
-                    wj1[h] = c_off[nd + 1];
+                    wj[h] = none_before ? (stays ? cj : cj + 1) : W.coff[nd];
+                    wj1[h] = W.coff[nd + 1];
                     kept[h] = none_before && stays;
                     act[h] = !kept[h];
                 } else {
