@@ -881,7 +881,9 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
 
 int build_survivor_cache(bn_table* t, cudaStream_t s)
 {
-    if (t->gcache || !t->amask || t->alive_total <= SURV_CAP_MAX || !(t->max_abs_survivor < FX_LIMIT)) return BN_OK;
+    // every pruned table whose entries fit the fixed point gets one (28 B per survivor):
+    // a many-network launch may keep fewer survivors in shared memory than one network does
+    if (t->gcache || !t->amask || t->alive_total < 1 || !(t->max_abs_survivor < FX_LIMIT)) return BN_OK;
     const int cap = (int)t->alive_total;
     uint8_t* g = nullptr;
     cudaError_t e = cudaMalloc((void**)&g, surv_cache_stride(cap));
@@ -1703,9 +1705,21 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
     BN_CUDA(cudaMemcpyAsync(d_states, hs.data(), sizeof(ChainState) * nf, cudaMemcpyHostToDevice, s));
     BN_CUDA(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, s));
     const unsigned blocks = (unsigned)base[nf];
+    // shared-memory survivor caches up to `limit` survivors: SURV_CAP_MAX, or less when that
+    // lets every block of the launch be resident at once (networks above the limit use
+    // their global-memory cache)
+    int limit = SURV_CAP_MAX;
+    {
+        const int per_sm = (int)((blocks + sm_count() - 1) / sm_count());
+        if (per_sm > 2) {
+            const long room = (long)(227 * 1024) / per_sm - (long)sizeof(FusedSmem) * BATCH_WARPS - 1024;
+            const long fit = (room - 4 * (MAXN + 1) - 16) / 28;
+            if (fit > 0) limit = (int)std::min<long>(limit, fit);
+        }
+    }
     int cap = 0;
     for (bn_chains* c : fused)
-        if (c->t->alive_total <= SURV_CAP_MAX && c->t->max_abs_survivor < FX_LIMIT)
+        if (c->t->alive_total <= limit && c->t->max_abs_survivor < FX_LIMIT)
             cap = std::max(cap, (int)c->t->alive_total);
     size_t smem = 0;
     {

@@ -28,7 +28,8 @@ struct bn_table {
     void* alive_block = nullptr;
     double max_abs_survivor = 0.0;   // largest |entry| among the survivors
     // the survivors in the fused sampler's cache layout (bn_mcmc.cu), in global memory, for
-    // networks whose survivors do not fit a block's shared memory (null otherwise)
+    // launches whose shared memory cannot hold them (null if the entries exceed its fixed
+    // point)
     uint8_t* gcache = nullptr;
     // full-scan tiling chosen by bn_table_autotune, per number of 256-item groups (1..8);
     // tuned_sub == 0: not tuned
@@ -44,8 +45,8 @@ int rank_entries(bn_table* t, cudaStream_t s);
 
 // Dominance pruning and the scan over the surviving entries (bn_prune.cu).
 int prune_table(bn_table* t, cudaStream_t s);
-// The survivors in the fused sampler's cache layout in global memory (t->gcache) when they
-// are too many for shared memory and their entries fit its fixed point (bn_mcmc.cu).
+// The survivors in the fused sampler's cache layout in global memory (t->gcache) when their
+// entries fit its fixed point (bn_mcmc.cu).
 int build_survivor_cache(bn_table* t, cudaStream_t s);
 int launch_scan_pruned(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc, uint32_t* list_best,
                        int cap, cudaStream_t s);
