@@ -148,8 +148,8 @@ def test_switching_mode_recaptures_the_step(gpu):
 
 def test_fused_steps_equal_batched_steps_uncached_survivors(gpu):
     """A network with more survivors than the shared-memory cache holds (little data: many
-    parent sets stay undominated) walks them in global memory; results must still equal
-    the per-step path on the full table, bit for bit."""
+    parent sets stay undominated) runs on the same cache layout in global memory; results
+    must still equal the per-step path on the full table, bit for bit."""
     ar = np.full(50, 3, np.uint8)
     net = synth.random_network(50, 3, ar, 0xB4E5_0B0B)
     data = synth.forward_sample(net, 250, 0xB4E5_0B0C)
@@ -164,4 +164,27 @@ def test_fused_steps_equal_batched_steps_uncached_survivors(gpu):
     gpu.chains_step(b, 250)
     for what in ("trace_score", "trace_accept", "orders", "ranks", "best_scores", "best_orders", "accepts",
                  "edge_counts"):
+        assert np.array_equal(gpu.chains_read(a, what), gpu.chains_read(b, what)), what
+
+
+@pytest.mark.parametrize("trace_cap", [0, 400])
+def test_fused_fallback_for_large_entries_equals_batched(gpu, trace_cap):
+    """Entries beyond the fused kernel's fixed-point range (|entry| >= 2^22; here every
+    entry shifted by -1e7, which changes no order and no dominance) take its fallback,
+    which re-scores every span node from the table's survivor arrays with FP64 changes."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    sc = gpu.table_scores(gpu.build_scores(data, arity, k, R=R)) - 1.0e7
+    t = gpu.table_from_scores(sc, k)
+    kw = dict(burn_in=30, trace_cap=trace_cap, record_every=5, record_cap=100)
+    a = gpu.chains_create(t, 32, 11, **kw)
+    gpu.chains_step(a, 400)                                  # batched, full scan
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    b = gpu.chains_create(t, 32, 11, **kw)
+    gpu.chains_step(b, 150)
+    gpu.chains_step(b, 250)
+    outs = ["orders", "scores", "ranks", "best_orders", "best_scores", "best_ranks", "accepts", "edge_counts",
+            "record", "steps", "items"]
+    if trace_cap:
+        outs += ["trace_score", "trace_accept"]
+    for what in outs:
         assert np.array_equal(gpu.chains_read(a, what), gpu.chains_read(b, what)), what
