@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--iters-per-step", type=int, default=1000,
                     help="MH iterations of every chain in one timed step")
-    ap.add_argument("--ess-steps", type=int, default=20000)
+    ap.add_argument("--ess-steps", type=int, default=40000)
     ap.add_argument("--ess-thin", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-ess", action="store_true")
