@@ -68,6 +68,29 @@ def test_batch_untraced_equals_full_scan_alone(gpu):
             assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
 
 
+def test_batch_of_many_blocks_equals_full_scan_alone(gpu):
+    """More blocks than fit two per SM: the launch caps its shared-memory survivor caches so
+    every block is resident, and networks above the cap run on their global-memory
+    caches; every network's results still equal stepping it alone on its full table."""
+    nets = _nets(20, 21)
+    tables = []
+    for data, ar, k in nets:
+        t = gpu.build_scores(data, ar, k)
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+        tables.append(t)
+    chains = [128] * len(tables)                  # 20 x 128 chains = 320 blocks of 8
+    seeds = [5 * i + 2 for i in range(len(tables))]
+    b = gpu.batch_create(tables, chains, seeds, burn_in=20)
+    b.step(300)
+    for i, t in enumerate(tables):
+        gpu.table_set_scan(t, gpu.SCAN_FULL)
+        alone = gpu.chains_create(t, chains[i], seeds[i], burn_in=20)
+        gpu.chains_step(alone, 300)
+        for what in ("orders", "scores", "best_scores", "best_orders", "best_ranks", "accepts", "edge_counts",
+                     "steps", "items"):
+            assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
+
+
 def test_batch_network_vs_oracle(gpu):
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     tab = oracle.build_table(data, arity, k, R=R)

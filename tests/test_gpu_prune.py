@@ -146,7 +146,8 @@ def test_switching_mode_recaptures_the_step(gpu):
     assert np.array_equal(gpu.chains_read(a, "trace_score"), gpu.chains_read(b, "trace_score"))
 
 
-def test_fused_steps_equal_batched_steps_uncached_survivors(gpu):
+@pytest.mark.parametrize("trace_cap", [400, 0])
+def test_fused_steps_equal_batched_steps_uncached_survivors(gpu, trace_cap):
     """A network with more survivors than the shared-memory cache holds (little data: many
     parent sets stay undominated) runs on the same cache layout in global memory; results
     must still equal the per-step path on the full table, bit for bit."""
@@ -154,7 +155,7 @@ def test_fused_steps_equal_batched_steps_uncached_survivors(gpu):
     net = synth.random_network(50, 3, ar, 0xB4E5_0B0B)
     data = synth.forward_sample(net, 250, 0xB4E5_0B0C)
     t = gpu.build_scores(data, ar, 4)
-    kw = dict(burn_in=20, trace_cap=400)
+    kw = dict(burn_in=20, trace_cap=trace_cap)
     a = gpu.chains_create(t, 32, 99, **kw)
     gpu.chains_step(a, 400)
     gpu.table_set_scan(t, gpu.SCAN_PRUNED)
@@ -162,8 +163,10 @@ def test_fused_steps_equal_batched_steps_uncached_survivors(gpu):
     b = gpu.chains_create(t, 32, 99, **kw)
     gpu.chains_step(b, 150)
     gpu.chains_step(b, 250)
-    for what in ("trace_score", "trace_accept", "orders", "ranks", "best_scores", "best_orders", "accepts",
-                 "edge_counts"):
+    outs = ["orders", "ranks", "scores", "best_scores", "best_orders", "best_ranks", "accepts", "edge_counts"]
+    if trace_cap:
+        outs += ["trace_score", "trace_accept"]
+    for what in outs:
         assert np.array_equal(gpu.chains_read(a, what), gpu.chains_read(b, what)), what
 
 
