@@ -282,6 +282,8 @@ struct FusedArgs {
     int cap;             // survivors per warp cache (shared-memory layout of the launch;
                          // the table's survivor count for a global-memory cache)
     const uint8_t* gcache;   // not staged: the same cache in global memory, or null
+    const uint16_t* gfirst;  // with gcache: [node][v] first survivor of the node whose set
+                             // contains node v (the node's survivor count if none)
     double margin_x;     // bound on |ln10 (dpart - (s' - s))| (rounding of the two sums)
     int64_t guard_fx;    // two order scores whose exact fixed-point sums differ by more than
                          // this (2^-32 units) compare the same way as their FP64 sums
@@ -437,6 +439,19 @@ __global__ void k_gcache_fill(const int64_t* __restrict__ keys, const uint32_t* 
     if (j <= (uint32_t)n) c_off[j] = j < (uint32_t)n ? aoff[j] : total;
 }
 
+__global__ void k_gcache_first(int n, int cap, const uint8_t* __restrict__ cache, uint16_t* __restrict__ first)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * 64) return;
+    const int nd = idx >> 6, v = idx & 63;
+    const uint64_t* c_mask = (const uint64_t*)cache;
+    const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)cap);
+    const uint32_t j0 = c_off[nd], j1 = c_off[nd + 1];
+    uint32_t j = j0;
+    while (j < j1 && ((c_mask[j] >> v) & 1ull) == 0ull) ++j;
+    first[idx] = (uint16_t)min(j - j0, 65535u);
+}
+
 __global__ void k_gcache_orb(int n, int cap, uint8_t* __restrict__ cache)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,7 +466,9 @@ __global__ void k_gcache_orb(int n, int cap, uint8_t* __restrict__ cache)
     }
 }
 
-template <bool STAGED>
+// JUMP (global-memory caches): `first` = F.gfirst, the first survivor of every node that
+// contains each node, where a restarted walk with one gained predecessor begins
+template <bool STAGED, bool JUMP = false>
 __device__ __forceinline__ void chain_fused_body(const ChainState& S, const FusedArgs& F, int c, int lane,
                                                  FusedSmem& W, const uint8_t* cache)
 {
@@ -577,7 +594,13 @@ __device__ __forceinline__ void chain_fused_body(const ChainState& S, const Fuse
                     cjv[h] = cj;
                     const bool none_before = (W.corb[nd] & gained) == 0ull;
                     const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
-                    wj[h] = none_before ? (stays ? cj : cj + 1) : W.coff[nd];
+                    uint32_t restart = W.coff[nd];
+                    if (JUMP && !none_before && (gained & (gained - 1)) == 0ull) {   // (gained != 0 here)
+                        // one gained predecessor v: survivors before the first one containing
+                        // v stay inconsistent (they were before the first consistent one)
+                        restart += F.gfirst[nd * 64 + (__ffsll((long long)gained) - 1)];
+                    }
+                    wj[h] = none_before ? (stays ? cj : cj + 1) : restart;
                     wj1[h] = W.coff[nd + 1];
                     kept[h] = none_before && stays;
                     act[h] = !kept[h];
@@ -845,7 +868,7 @@ __global__ void __launch_bounds__(32 * FUSED_WARPS) k_chain_fused(ChainState S, 
         __syncthreads();
     }
     if (c >= S.C) return;
-    chain_fused_body<MODE != 0>(S, F, c, lane, sm[warp], MODE == 2 ? F.gcache : fcache);
+    chain_fused_body<MODE != 0, MODE == 2>(S, F, c, lane, sm[warp], MODE == 2 ? F.gcache : fcache);
 }
 
 // many networks' chains in one launch: block g belongs to the network i with
@@ -875,7 +898,7 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
     const int64_t c = (g - cta_base[lo]) * BATCH_WARPS + warp;
     if (c >= S.C) return;
     if (F.staged) chain_fused_body<true>(S, F, (int)c, lane, sm[warp], fcache);
-    else if (F.gcache) chain_fused_body<true>(S, F, (int)c, lane, sm[warp], F.gcache);
+    else if (F.gcache) chain_fused_body<true, true>(S, F, (int)c, lane, sm[warp], F.gcache);
     else chain_fused_body<false>(S, F, (int)c, lane, sm[warp], fcache);
 }
 
@@ -886,7 +909,8 @@ int build_survivor_cache(bn_table* t, cudaStream_t s)
     if (t->gcache || !t->amask || t->alive_total < 1 || !(t->max_abs_survivor < FX_LIMIT)) return BN_OK;
     const int cap = (int)t->alive_total;
     uint8_t* g = nullptr;
-    cudaError_t e = cudaMalloc((void**)&g, surv_cache_stride(cap));
+    // the cache, then the [n][64] first-survivor table (16-bit offsets within a node)
+    cudaError_t e = cudaMalloc((void**)&g, surv_cache_stride(cap) + sizeof(uint16_t) * 64 * MAXN);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return BN_OK;                       // no cache: the uncached walk still works
@@ -897,6 +921,8 @@ int build_survivor_cache(bn_table* t, cudaStream_t s)
     BN_LAUNCH_CHECK("k_gcache_fill");
     k_gcache_orb<<<(t->n + 63) / 64, 64, 0, s>>>(t->n, cap, g);
     BN_LAUNCH_CHECK("k_gcache_orb");
+    k_gcache_first<<<(t->n * 64 + 255) / 256, 256, 0, s>>>(t->n, cap, g, (uint16_t*)(g + surv_cache_stride(cap)));
+    BN_LAUNCH_CHECK("k_gcache_first");
     t->gcache = g;
     return BN_OK;
 }
@@ -1154,6 +1180,7 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     F.iters = iters;
     F.staged = ch->t->alive_total <= SURV_CAP_MAX && ch->t->max_abs_survivor < FX_LIMIT ? 1 : 0;
     F.gcache = F.staged ? nullptr : ch->t->gcache;
+    F.gfirst = F.gcache ? (const uint16_t*)(F.gcache + surv_cache_stride((int)ch->t->alive_total)) : nullptr;
     F.cap = (F.staged || F.gcache) ? (int)ch->t->alive_total : 0;
     F.margin_x = mh_margin(ch->S.n, ch->t->max_abs_survivor);
     F.guard_fx = score_guard_fx(ch->S.n, ch->t->max_abs_survivor);
@@ -1744,6 +1771,7 @@ extern "C" int bn_batch_step(bn_batch* b, int64_t steps, void* stream)
             f.iters = it;
             f.staged = t->alive_total <= cap && t->max_abs_survivor < FX_LIMIT ? 1 : 0;
             f.gcache = f.staged ? nullptr : t->gcache;
+            f.gfirst = f.gcache ? (const uint16_t*)(f.gcache + surv_cache_stride((int)t->alive_total)) : nullptr;
             f.cap = f.gcache ? (int)t->alive_total : cap;
             f.margin_x = mh_margin(t->n, t->max_abs_survivor);
             f.guard_fx = score_guard_fx(t->n, t->max_abs_survivor);
