@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
             const int pairs = (int)min((int64_t)SCAN_SUB, e1 - base) >> 1;
             const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
             const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
-#pragma unroll 16
+#pragma unroll 32
             for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
                 const uint2 pp = P[j];
                 const uint4 mm = ((const uint4*)M)[j];
