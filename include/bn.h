@@ -160,7 +160,9 @@ int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
  *                   its set lies in a node's predecessors so does the subset, which has
  *                   a score at least as high and a lower rank.  Results are identical.
  *                   The surviving entries are kept in score order, so each order stops
- *                   at its first consistent one.  The first switch builds them (k <= 7).
+ *                   at its first consistent one.  The first switch builds them (k <= 7),
+ *                   with a copy laid out for the fused sampler (28 B per survivor plus
+ *                   8 KB, device memory owned by the table).
  *   BN_SCAN_UNRANK  every entry, as BN_SCAN_FULL, but each parent set is computed from
  *                   its rank on the fly (the paper's first strategy, Sec. V.B / Algorithm
  *                   2, in this library's size-ascending combinatorial number system)
