@@ -1,16 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the order-space MH sampler (Algorithm 1) on one GB300.
 
-One step = one Metropolis-Hastings iteration of every chain: a swap proposal per chain,
-the order score of Eq. (6) of every proposed order (an exact full-order score; only the
-nodes between the swapped positions are re-scanned, the others keep their best sets),
-the MH test, best-graph and edge-count updates -- kernels replayed from a CUDA graph.
+An MH iteration of a chain: a swap proposal, the order score of Eq. (6) of the proposed
+order (an exact full-order score; only the nodes between the swapped positions are
+re-scored, the others keep their best sets), the MH test, best-graph and edge-count
+updates.  A timed step is --iters-per-step (default 1,000) iterations of every chain.
 Workload: 60 ternary nodes, in-degree <= 3, m = 1000 synthetic samples, k = 4 (489,406
 parent sets per node, 29.36 M FP64 entries, 235 MB), 256 chains.
 
-The headline runs the pruned scan (only table entries that no subset of their parent set
-matches or beats are tested -- the same results, see include/bn.h); the full-table scan
-is timed beside it with its own roofline.  Edge-posterior ESS/s of the plain uniform-swap
+The headline runs the pruned table (only entries that no subset of their parent set
+matches or beats -- the same results, see include/bn.h) in the fused sampler, one launch
+per timed step; the full-table scan (three kernels per iteration, replayed from a CUDA
+graph) is timed beside it with its own roofline.  Edge-posterior ESS/s of the plain uniform-swap
 sampler and of the learned-proposal sampler (trained on the plain sampler's history) are
 measured on the same table.
 
