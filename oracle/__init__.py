@@ -7,6 +7,7 @@ The C library is compiled with gcc on first use (or by ``build()``) next to this
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes as C
 import os
 import subprocess
@@ -54,7 +55,7 @@ _dp = C.POINTER(C.c_double)
 
 class MCMCParams(C.Structure):
     _fields_ = [("chains", C.c_int), ("iters", C.c_int64), ("burn_in", C.c_int64),
-                ("seed", C.c_uint64), ("literal_log", C.c_int)]
+                ("seed", C.c_uint64), ("literal_log", C.c_int), ("chain0", C.c_int)]
 
 
 def _declare(L):
@@ -75,6 +76,9 @@ def _declare(L):
                                   C.c_int, C.c_double, C.c_double, _dp]
     L.orc_ppf.restype = C.c_double
     L.orc_ppf.argtypes = [C.c_double]
+    L.orc_build_table_node.restype = None
+    L.orc_build_table_node.argtypes = [_u8p, C.c_int, C.c_int, _u8p, C.c_int, C.c_int,
+                                       C.c_double, C.c_double, _dp, C.c_int, _dp]
     L.orc_build_table.restype = None
     L.orc_build_table.argtypes = [_u8p, C.c_int, C.c_int, _u8p, C.c_int, C.c_int,
                                   C.c_double, C.c_double, _dp, _dp]
@@ -166,15 +170,34 @@ def ppf(r):
     return float(lib().orc_ppf(r))
 
 
-def build_table(data, arity, k, kind=0, ess=1.0, log10_gamma=0.0, R=None):
+def _threads(threads):
+    """Host threads for the calls below: None = every core.  The C calls release the
+    GIL, so each thread runs the unmodified single-threaded oracle on its share."""
+    return max(1, threads if threads else (os.cpu_count() or 1))
+
+
+def build_table(data, arity, k, kind=0, ess=1.0, log10_gamma=0.0, R=None, threads=1):
+    """Every entry of the table; with threads > 1 (None = all cores) the nodes are
+    built by orc_build_table_node in parallel threads (the same entries)."""
     data = _c(data, np.uint8)
     arity = _c(arity, np.uint8)
     m, n = data.shape
     S = num_sets(n - 1, k)
     out = np.zeros((n, S), np.float64)
     Rp = _c(R, np.float64) if R is not None else None
-    lib().orc_build_table(_p(data, _u8p), m, n, _p(arity, _u8p), k, kind, ess,
-                          log10_gamma, _p(Rp, _dp), _p(out, _dp))
+    nt = _threads(threads)
+    if nt == 1:
+        lib().orc_build_table(_p(data, _u8p), m, n, _p(arity, _u8p), k, kind, ess,
+                              log10_gamma, _p(Rp, _dp), _p(out, _dp))
+        return out
+    L = lib()
+
+    def node(i):
+        L.orc_build_table_node(_p(data, _u8p), m, n, _p(arity, _u8p), k, kind, ess,
+                               log10_gamma, _p(Rp, _dp), i, _p(out[i], _dp))
+
+    with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+        list(ex.map(node, range(n)))
     return out
 
 
@@ -194,6 +217,24 @@ def order_score(table, k, order):
     br = np.zeros(n, np.uint32)
     s = lib().orc_order_score(_p(table, _dp), n, k, _p(order, _u8p), _p(br, _u32p))
     return float(s), br
+
+
+def order_scores(table, k, orders, threads=None):
+    """order_score of every row of ``orders`` (B x n), the rows spread over host threads
+    (None = all cores); returns (B scores, B x n best ranks)."""
+    table = _c(table, np.float64)
+    orders = _c(orders, np.uint8)
+    B, n = orders.shape
+    sc = np.zeros(B, np.float64)
+    br = np.zeros((B, n), np.uint32)
+    L = lib()
+
+    def one(b):
+        sc[b] = L.orc_order_score(_p(table, _dp), n, k, _p(orders[b], _u8p), _p(br[b], _u32p))
+
+    with cf.ThreadPoolExecutor(max_workers=_threads(threads)) as ex:
+        list(ex.map(one, range(B)))
+    return sc, br
 
 
 def order_score_sum(table, k, order):
@@ -243,10 +284,12 @@ def pair_decode(n, idx):
 
 
 def mcmc_run(table, k, chains, iters, seed, burn_in=0, init_orders=None, trace=False,
-             literal_log=False):
+             literal_log=False, threads=1, chain0=0):
+    """orc_mcmc_run of chains chain0 .. chain0 + chains - 1; with threads > 1 (None = all
+    cores) the chains are split into contiguous groups run in parallel threads, each
+    group one orc_mcmc_run call with its own chain0 (the same results as one call)."""
     table = _c(table, np.float64)
     n = table.shape[0]
-    P = MCMCParams(chains, iters, burn_in, seed, 1 if literal_log else 0)
     io = _c(init_orders, np.uint8) if init_orders is not None else None
     out = dict(
         final_orders=np.zeros((chains, n), np.uint8),
@@ -259,11 +302,26 @@ def mcmc_run(table, k, chains, iters, seed, burn_in=0, init_orders=None, trace=F
     )
     ts = np.zeros((chains, iters), np.float64) if trace else None
     ta = np.zeros((chains, iters), np.uint8) if trace else None
-    lib().orc_mcmc_run(_p(table, _dp), n, k, C.byref(P), _p(io, _u8p),
-                       _p(out["final_orders"], _u8p), _p(out["final_score"], _dp),
-                       _p(out["best_order"], _u8p), _p(out["best_score"], _dp),
-                       _p(out["best_rank"], _u32p), _p(out["edge_counts"], _u64p),
-                       _p(out["accepts"], _i64p), _p(ts, _dp), _p(ta, _u8p))
+    L = lib()
+
+    def group(lo, hi):
+        if hi <= lo:
+            return
+        P = MCMCParams(hi - lo, iters, burn_in, seed, 1 if literal_log else 0, chain0 + lo)
+        sl = lambda a: a[lo:hi] if a is not None else None      # noqa: E731 (contiguous rows)
+        L.orc_mcmc_run(_p(table, _dp), n, k, C.byref(P), _p(sl(io), _u8p),
+                       _p(sl(out["final_orders"]), _u8p), _p(sl(out["final_score"]), _dp),
+                       _p(sl(out["best_order"]), _u8p), _p(sl(out["best_score"]), _dp),
+                       _p(sl(out["best_rank"]), _u32p), _p(sl(out["edge_counts"]), _u64p),
+                       _p(sl(out["accepts"]), _i64p), _p(sl(ts), _dp), _p(sl(ta), _u8p))
+
+    nt = min(_threads(threads), max(chains, 1))
+    if nt == 1:
+        group(0, chains)
+    else:
+        cuts = [chains * g // nt for g in range(nt + 1)]
+        with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+            list(ex.map(lambda g: group(cuts[g], cuts[g + 1]), range(nt)))
     if trace:
         out["trace_score"] = ts
         out["trace_accept"] = ta

@@ -204,6 +204,20 @@ double orc_local_score(const uint8_t* data, int m, int n, const uint8_t* arity,
     return ls;
 }
 
+/* Preprocessing of Sec. III.A for one node: every local score of node i, by rank. */
+void orc_build_table_node(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                          int kind, double ess, double log10_gamma, const double* R,
+                          int i, double* row)
+{
+    int64_t S = orc_num_sets(n - 1, k);
+    int slots[64], parents[64];
+    for (int64_t rho = 0; rho < S; ++rho) {
+        int j = orc_unrank(n - 1, k, rho, slots);
+        for (int t = 0; t < j; ++t) parents[t] = orc_cand_to_node(i, slots[t]);
+        row[rho] = orc_local_score(data, m, n, arity, i, parents, j, kind, ess, log10_gamma, R);
+    }
+}
+
 /* Preprocessing of Sec. III.A: every local score of every (node, parent set), stored
  * here densely by (node, rank) instead of in a hash table. */
 void orc_build_table(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
@@ -211,15 +225,9 @@ void orc_build_table(const uint8_t* data, int m, int n, const uint8_t* arity, in
                      double* table)
 {
     int64_t S = orc_num_sets(n - 1, k);
-    int slots[64], parents[64];
-    for (int i = 0; i < n; ++i) {
-        for (int64_t rho = 0; rho < S; ++rho) {
-            int j = orc_unrank(n - 1, k, rho, slots);
-            for (int t = 0; t < j; ++t) parents[t] = orc_cand_to_node(i, slots[t]);
-            table[(size_t)i * (size_t)S + (size_t)rho] =
-                orc_local_score(data, m, n, arity, i, parents, j, kind, ess, log10_gamma, R);
-        }
-    }
+    for (int i = 0; i < n; ++i)
+        orc_build_table_node(data, m, n, arity, k, kind, ess, log10_gamma, R, i,
+                             table + (size_t)i * (size_t)S);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -370,6 +378,7 @@ static uint64_t orc_mulhi(uint64_t a, uint64_t b)
  *     order[floor(x * (i+1) / 2^64)], x the next 64-bit word of the stream of blocks
  *     Philox(ctr = {j, c, 1, 0}), j = 0, 1, ...; identity start.
  *   step t of chain c: x = Philox(ctr = {t, c, 0, 0});
+ *     (chain c of a call is chain p->chain0 + c of these streams)
  *     pair index floor(x0 * P / 2^64), P = n(n-1)/2, pairs (a<b) in lexicographic order;
  *     u = ((x1 >> 12) + 0.5) * 2^-52 in (0, 1). */
 void orc_init_order(uint64_t seed, int chain, int n, uint8_t* order)
@@ -422,8 +431,9 @@ void orc_mcmc_run(const double* table, int n, int k, const orc_mcmc_params* p,
     uint32_t cur_r[64], prop_r[64], best_r[64];
     int slots[64];
     for (int c = 0; c < p->chains; ++c) {
+        const uint64_t cg = (uint64_t)p->chain0 + (uint64_t)c;    /* the chain's stream */
         if (init_orders) memcpy(cur, init_orders + (size_t)c * (size_t)n, (size_t)n);
-        else orc_init_order(p->seed, c, n, cur);
+        else orc_init_order(p->seed, (int)cg, n, cur);
         double s = orc_order_score(table, n, k, cur, cur_r);
         double bs = s;
         memcpy(best, cur, (size_t)n);
@@ -432,7 +442,7 @@ void orc_mcmc_run(const double* table, int n, int k, const orc_mcmc_params* p,
         uint64_t* E = edge_counts ? edge_counts + (size_t)c * (size_t)n * (size_t)n : NULL;
         if (E) memset(E, 0, sizeof(uint64_t) * (size_t)n * (size_t)n);
         for (int64_t t = 0; t < p->iters; ++t) {
-            uint64_t ctr[4] = {(uint64_t)t, (uint64_t)c, 0, 0};
+            uint64_t ctr[4] = {(uint64_t)t, cg, 0, 0};
             uint64_t x[4];
             orc_philox4x64(ctr, key, x);
             int a, b;

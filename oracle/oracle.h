@@ -42,6 +42,10 @@ double orc_local_score(const uint8_t* data, int m, int n, const uint8_t* arity,
                        int child, const int* parents, int np, int kind, double ess,
                        double log10_gamma, const double* R);
 double orc_ppf(double r);
+/* one node's row of the table (S(n-1,k) entries, rank order) */
+void   orc_build_table_node(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                            int kind, double ess, double log10_gamma, const double* R,
+                            int i, double* row);
 /* all n * S(n-1,k) entries, node-major, rank order (candidate space of each node) */
 void   orc_build_table(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
                        int kind, double ess, double log10_gamma, const double* R,
@@ -74,6 +78,8 @@ typedef struct {
     int64_t  burn_in;
     uint64_t seed;
     int      literal_log;     /* 1: accept iff ln u < delta (un-scaled), as printed */
+    int      chain0;          /* chain c of the call draws the Philox streams of chain
+                                 chain0 + c (lets chains run in separate calls)      */
 } orc_mcmc_params;
 
 /* init_orders: chains x n (NULL = draw from the Philox init stream);

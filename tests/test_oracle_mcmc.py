@@ -136,3 +136,26 @@ def test_ess_known_autocorrelation():
         s[t] = 1 - s[t - 1] if u[t] < p else s[t - 1]
     lam = 1 - 2 * p
     assert oracle.ess(s) == pytest.approx(T * (1 - lam) / (1 + lam), rel=0.2)
+
+
+def test_threaded_runs_equal_one_call():
+    """The oracle's host-thread split (chains in contiguous groups, each group one call
+    drawing the Philox streams of its own chain indices; the table's nodes in parallel)
+    gives exactly what one single-threaded call gives."""
+    data, arity, k, R, _ = synth.workload("n6_k2_m100")
+    tab = oracle.build_table(data, arity, k, R=R)
+    assert np.array_equal(tab, oracle.build_table(data, arity, k, R=R, threads=3))
+    one = oracle.mcmc_run(tab, k, 7, 150, seed=11, burn_in=30, trace=True)
+    for nt in (2, 3, 7):
+        par = oracle.mcmc_run(tab, k, 7, 150, seed=11, burn_in=30, trace=True, threads=nt)
+        for key in one:
+            assert np.array_equal(one[key], par[key]), (nt, key)
+    # chain0 selects the streams: chains 3..6 alone equal rows 3..6 of the full run
+    tail = oracle.mcmc_run(tab, k, 4, 150, seed=11, burn_in=30, trace=True, chain0=3)
+    for key in one:
+        assert np.array_equal(one[key][3:], tail[key]), key
+    orders = synth.random_orders(6, 9, 2)
+    sc, br = oracle.order_scores(tab, k, orders, threads=4)
+    for b in range(9):
+        s, r = oracle.order_score(tab, k, orders[b])
+        assert sc[b] == s and np.array_equal(br[b], r)
