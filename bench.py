@@ -530,7 +530,7 @@ def main():
                      "note": "the paper's scan (a6) over the full table for a step of all chains' orders, timed "
                              "in this run (full_scan); the headline step runs the pruned fused sampler "
                              "k_chain_fused instead, which is latency-bound (one warp per chain, under two "
-                             "warps per SM; see pruned_step and profiles/k_chain_fused_n60_256chains.md)"}
+                             "warps per SM; see pruned_step)"}
         avg_fused = fused_ms / max(fused_l, 1)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:

@@ -142,11 +142,13 @@ int bn_score_orders_sum(const bn_table* t, const uint8_t* orders, int B, double*
  * (about 8 MiB / (12 n) orders: 11,600 at n = 60), larger B returns BN_EINVAL with the
  * limit in the message.  Nothing is allocated or freed: no cudaMalloc, cudaFree or
  * allocating library routine.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  All calls share the one array and it keeps the previous call's
- * contents (the call clears what must start at zero), so calls that overlap on the GPU
- * (other streams, other host threads) race: serialise them.
+ * The first call on each device (and the first after that device's CUDA context was
+ * destroyed and created again) looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  Every call waits for its stream
+ * (it reads a status word back), so it must not be made while the stream is being
+ * captured.  All calls share the one array and it keeps the previous call's contents
+ * (the call clears what must start at zero), so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them.
  * Errors: as bn_score_orders. */
 int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
                             uint32_t* best_rank, double* order_score, void* stream);

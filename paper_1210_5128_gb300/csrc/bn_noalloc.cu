@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "bn_table.cuh"
 
 namespace bn {
@@ -20,47 +22,60 @@ static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;   // 8 MiB
 static __device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // Per-device address of g_noalloc_scratch.  In host code the array's name is only a
-// host-side stand-in for the symbol, never a device address, so it is resolved once per
-// device with that device current.
+// host-side stand-in for the symbol, never a device address, so the address is looked up
+// with the device current and kept per device together with the identity of the CUDA
+// context it belongs to: a context destroyed and created again (cudaDeviceReset, or the
+// primary context released and retained anew) has a new identity, and the address is
+// looked up again.  Without the driver's context identity the lookup runs on every call.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+struct NoallocSlot {
+    unsigned long long ctx = 0;
+    void* ptr = nullptr;
+};
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[64] = {nullptr};
+static NoallocSlot g_noalloc_slot[64];
+
+// identity of the calling thread's current context (false: not available)
+static bool current_context_id(unsigned long long* id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    return get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, id) == CUDA_SUCCESS;
+}
 
 static int noalloc_scratch(void** out)
 {
     const int d = device_id();
     if (d < 0 || d >= 64) return set_error(BN_EUNSUPPORTED, "bn_score_orders_noalloc: device id %d", d);
+    unsigned long long ctx = 0;
+    const bool known = current_context_id(&ctx);
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[d]) {
+    NoallocSlot& slot = g_noalloc_slot[d];
+    if (!known || !slot.ptr || slot.ctx != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-        g_noalloc_ptr[d] = p;
+        slot.ctx = ctx;
+        slot.ptr = p;
     }
-    *out = g_noalloc_ptr[d];
+    *out = slot.ptr;
     return BN_OK;
-}
-
-__global__ void k_noalloc_reduce(const uint32_t* __restrict__ list_best, const uint32_t* __restrict__ srank,
-                                 const int64_t* __restrict__ keys, int64_t Sp, int n, int B,
-                                 uint32_t* __restrict__ best_rank, double* __restrict__ score)
-{
-    __shared__ int64_t s_key[8][MAXN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (b >= B) return;
-    for (int i = lane; i < n; i += 32) {
-        uint32_t p = list_best[(size_t)i * B + b];
-        if ((int64_t)p >= Sp) p = 0;                  // only after a timed-out scan
-        const uint32_t r = srank[(size_t)i * Sp + p];
-        s_key[warp][i] = keys[(size_t)i * Sp + r];
-        if (best_rank) best_rank[(size_t)b * n + i] = r;
-    }
-    __syncwarp();
-    if (lane == 0 && score) {
-        double sum = 0.0;
-        for (int i = 0; i < n; ++i) sum = __dadd_rn(sum, key_to_double(s_key[warp][i]));
-        score[b] = sum;
-    }
 }
 
 }  // namespace bn
@@ -107,8 +122,7 @@ extern "C" int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders,
     rc = scan_nodes_fits(t, B) ? launch_scan_nodes(t, B, d_pc, d_best, d_status, s)
                                : launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_status, s);
     if (rc) return rc;
-    k_noalloc_reduce<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, best_rank, order_score);
-    BN_LAUNCH_CHECK("k_noalloc_reduce");
+    if ((rc = launch_reduce_orders(t, d_best, B, best_rank, order_score, s))) return rc;
     uint32_t st = 0;
     BN_CUDA(cudaMemcpyAsync(&st, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     BN_CUDA(cudaStreamSynchronize(s));

@@ -518,6 +518,14 @@ __global__ void k_reduce_orders(const uint32_t* __restrict__ list_best, const ui
     }
 }
 
+int launch_reduce_orders(const bn_table* t, const uint32_t* list_best, int B, uint32_t* best_rank, double* score,
+                         cudaStream_t s)
+{
+    k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(list_best, t->srank, t->keys, t->Sp, t->n, B, best_rank, score);
+    BN_LAUNCH_CHECK("k_reduce_orders");
+    return BN_OK;
+}
+
 }  // namespace bn
 
 using namespace bn;
@@ -596,8 +604,7 @@ static int score_orders_impl(const bn_table* t, const uint8_t* orders, int B, ui
                                : launch_scan(t, pl, d_cnt, d_pc, d_best, B, d_st, s);
     if (rc) return rc;
     if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
-    k_reduce_orders<<<(B + 7) / 8, 256, 0, s>>>(d_best, t->srank, t->keys, t->Sp, n, B, d_rank, d_score);
-    BN_LAUNCH_CHECK("k_reduce_orders");
+    if ((rc = launch_reduce_orders(t, d_best, B, d_rank, d_score, s))) return rc;
     if (mem == BN_MEM_HOST) {
         if (best_rank)
             BN_CUDA(cudaMemcpyAsync(best_rank, d_rank, sizeof(uint32_t) * (size_t)B * n, cudaMemcpyDeviceToHost, s));

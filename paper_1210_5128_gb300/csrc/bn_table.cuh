@@ -81,6 +81,12 @@ int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_
 int launch_pred_lists(const uint8_t* orders, int B, int n, uint64_t* list_pc, uint32_t* list_best,
                       uint32_t* list_count, uint32_t* status, cudaStream_t s);
 
+// a7: per order b, the chosen rank of every node (best_rank[b * n + i], may be null) and
+// the FP64 sum over nodes, ascending node id, of their entries (score[b], may be null),
+// from the scan's smallest sorted positions list_best[i * B + b]
+int launch_reduce_orders(const bn_table* t, const uint32_t* list_best, int B, uint32_t* best_rank, double* score,
+                         cudaStream_t s);
+
 // best rank and FP64 entry of (node i, sorted position p)
 __device__ __forceinline__ uint32_t spos_rank(const bn_table& t, int i, uint32_t p)
 {

@@ -133,6 +133,10 @@ WORKLOADS = {
     "n40_k4_m2000": dict(n=40, arity=3, max_indeg=3, m=2000, k=4, prior=None, seed_index=2),
     # 60 ternary nodes, 1000 samples, k = 4 (the paper's largest graph)
     "n60_k4_m1000": dict(n=60, arity=3, max_indeg=3, m=1000, k=4, prior=None, seed_index=3),
+    # the n = 40 and n = 60 table shapes (k = 4) on binary data with 200 samples: tables the
+    # CPU oracle builds in seconds on a few host threads, for the full-size parity tests
+    "n40_k4_m200_bin": dict(n=40, arity=2, max_indeg=3, m=200, k=4, prior=None, seed_index=6),
+    "n60_k4_m200_bin": dict(n=60, arity=2, max_indeg=3, m=200, k=4, prior=None, seed_index=7),
 }
 
 

@@ -13,7 +13,7 @@ OUTS = ("trace_score", "trace_accept", "orders", "scores", "best_scores", "best_
         "edge_counts", "steps", "items")
 
 
-def _nets(count, seed, nmax=24):
+def _nets(count, seed, nmax=60):
     out = []
     rng = np.random.default_rng(seed)
     for t in range(count):
@@ -28,6 +28,7 @@ def _nets(count, seed, nmax=24):
 
 def test_batch_equals_networks_alone(gpu):
     nets = _nets(7, 3)
+    assert max(d.shape[1] for d, _, _ in nets) > 33          # spans beyond one warp's lanes
     tables = []
     for data, ar, k in nets:
         t = gpu.build_scores(data, ar, k)

@@ -10,8 +10,10 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _check_shared(gpu, tab, k, orders):
+def _check_shared(gpu, tab, k, orders, mode=None):
     t = gpu.table_from_scores(tab, k)
+    if mode is not None:
+        gpu.table_set_scan(t, mode)
     br, sc = gpu.score_orders(t, orders)
     for b, o in enumerate(orders):
         s_ref, r_ref = oracle.order_score(tab, k, o)
@@ -169,6 +171,27 @@ def test_unranked_parent_sets_equal_the_table(gpu, name, B):
     br_u, sc_u = gpu.score_orders(t, orders)
     assert np.array_equal(br_f, br_u)
     assert np.array_equal(sc_f, sc_u)
+
+
+@pytest.mark.parametrize("name,B", [("n6_k2_m100", 37), ("n20_k4_m1000", 5), ("n20_k4_m1000", 300)])
+def test_unranked_parent_sets_against_oracle(gpu, name, B):
+    """BN_SCAN_UNRANK (Algorithm 2's strategy: every parent set computed from its index
+    in the scan) on the oracle's table against the oracle's brute-force order score."""
+    data, arity, k, R, _ = synth.workload(name)
+    tab = oracle.build_table(data, arity, k, R=R)
+    _check_shared(gpu, tab, k, synth.random_orders(data.shape[1], B, 55 + B), mode=gpu.SCAN_UNRANK)
+
+
+def test_unranked_n40_against_oracle(gpu):
+    """The unranked scan at the n = 40 table shape (k = 4) on the oracle's table."""
+    data, arity, k, R, _ = synth.workload("n40_k4_m200_bin")
+    tab = oracle.build_table(data, arity, k, R=R, threads=None)
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_UNRANK)
+    orders = synth.random_orders(40, 64, 4)
+    br, sc = gpu.score_orders(t, orders)
+    sc_ref, br_ref = oracle.order_scores(tab, k, orders[:16])
+    assert np.array_equal(br[:16], br_ref) and np.array_equal(sc[:16], sc_ref)
 
 
 def test_unranked_sampler_equals_table_sampler(gpu):

@@ -42,6 +42,24 @@ def test_noalloc_matches_score_orders_on_two_calls(gpu):
         assert np.array_equal(score, ref_score)
 
 
+@pytest.mark.parametrize("mode,B", [("full", 8), ("pruned", 64), ("unrank", 64)])
+def test_noalloc_every_scan_path(gpu, mode, B):
+    """The kernels the call can dispatch to: the few-order scan (n * B <= 256), the scan
+    over the pruned table's survivors and the scan that unranks parent sets on the fly;
+    two calls in a row, each equal to bn_score_orders on the same table and mode."""
+    import torch
+    bn = gpu
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t = bn.build_scores(data, arity, k, R=R)
+    bn.table_set_scan(t, {"full": bn.SCAN_FULL, "pruned": bn.SCAN_PRUNED, "unrank": bn.SCAN_UNRANK}[mode])
+    for seed in (5, 6):
+        orders = synth.random_orders(20, B, seed)
+        ref_rank, ref_score = bn.score_orders(t, orders)
+        rank, score = _noalloc(bn, t, torch.as_tensor(orders, device="cuda"), torch)
+        assert np.array_equal(rank, ref_rank)
+        assert np.array_equal(score, ref_score)
+
+
 def test_noalloc_full_size_and_limit(gpu):
     import torch
     bn = gpu
