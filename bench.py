@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--no-ess", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven 96-network batch")
     ap.add_argument("--batch-iters", type=int, default=2048)
+    ap.add_argument("--batch-ess-steps", type=int, default=4000)
+    ap.add_argument("--batch-train", type=int, default=300)
     ap.add_argument("--no-accuracy", action="store_true", help="skip the ROC and noise study")
+    ap.add_argument("--no-configs", action="store_true", help="skip the n=20 and n=40 configurations")
     return ap.parse_args()
 
 
@@ -134,47 +137,52 @@ def _standin_table():
     return rng.standard_normal((n, oracle.num_sets(n - 1, k))) * 10.0 - 500.0, k
 
 
-def oracle_sample(seconds):
+def oracle_sample(seconds, threads=1):
     """The oracle's sampler (Algorithm 1: a full order score per iteration) at n = 60,
-    k = 4, run in short single-chain batches until ``seconds`` have passed."""
+    k = 4, run in short chains until ``seconds`` have passed; with threads > 1 the chains
+    of a round run in parallel host threads (each the unmodified single-threaded oracle).
+    Returns (order evaluations/s, evaluations, seconds, threads)."""
     import oracle
     tab, k = _standin_table()
     done, c, t0 = 0, 0, time.perf_counter()
     while True:
-        oracle.mcmc_run(tab, k, 1, 4, seed=1000 + c)
-        done += 5                 # the initial order + 4 proposals
-        c += 1
+        oracle.mcmc_run(tab, k, threads, 4, seed=1000, chain0=c, threads=threads)
+        done += 5 * threads       # per chain: the initial order + 4 proposals
+        c += threads
         el = time.perf_counter() - t0
         if el >= seconds:
-            return done / el, done, el
+            return done / el, done, el, threads
 
 
 def run_reference(args):
-    """Reference arm: the oracle as it stands on one host core.  One step = one order
-    evaluation (Eq. 6 by the oracle's brute-force subset walk) of a random order of the
-    n = 60, k = 4 workload."""
+    """Reference arm: the oracle as it stands on the host's cores.  One step = one order
+    evaluation (Eq. 6 by the oracle's brute-force subset walk) per host thread, each thread
+    running the unmodified single-threaded oracle on its own random order of the n = 60,
+    k = 4 workload."""
     import oracle
     import synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     tab, k = _standin_table()
-    orders = synth.random_orders(60, args.steps + 2, 4242)
-    for i in range(min(args.warmup, 2)):
-        oracle.order_score(tab, k, orders[i])
+    nt = os.cpu_count() or 1
+    orders = synth.random_orders(60, (args.steps + 2) * nt, 4242)
+    for i in range(min(args.warmup, 1)):
+        oracle.order_scores(tab, k, orders[:nt], threads=nt)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        oracle.order_score(tab, k, orders[2 + i])
+        oracle.order_scores(tab, k, orders[(i + 1) * nt:(i + 2) * nt], threads=nt)
     tot = time.perf_counter() - t0
-    value = args.steps / tot
+    value = args.steps * nt / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(args.chains),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} order evaluations ({tot:.1f} s) by the oracle at n=60, k=4, "
-                                   "one per step, on a seeded stand-in table of the workload's shape"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                         "sample": f"{args.steps * nt} order evaluations ({tot:.1f} s) by the oracle at n=60, "
+                                   f"k=4, {nt} per step (one per host thread), on a seeded stand-in table of "
+                                   "the workload's shape"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -192,9 +200,14 @@ def config_dict(chains, scan="pruned"):
                   "plus the 3.9 MB mask table per pass"}
 
 
-ALU_LANES_PER_SM = 64      # 32-bit logic / compare / min-max results per clock per SM
-SCAN_ALU_OPS = 3           # per (entry, item) test: 64-bit AND-NOT + zero test (2), min (1)
 L2_FLUSH_BYTES = 512 << 20 # written, then another buffer read, between timed steps (L2 is 129 MB)
+SCORE_B = (1, 2, 4, 8, 16, 64, 256, 1024)   # orders per bn_score_orders call in the scoring sweep
+ISSUE_PER_SM = 4           # warp schedulers per SM, one warp instruction per clock each
+# ncu smsp__inst_executed.sum of k_chain_fused<1> at this workload (256 chains, 1,000-step
+# launches), per chain per MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum
+# per launch of the full-table k_scan<1024,0> (256 items per node, the sampler's step)
+FUSED_INST_PER_CHAIN_STEP = 418.0
+SCAN_TRAFFIC_BYTES = 121.5e6
 
 
 def _flush_l2(torch, flush, stream):
@@ -294,6 +307,126 @@ def _ess_run(bn, torch, table, chains, seed, pre_steps, steps, stream, net=None,
                 train_seconds=t_train), f
 
 
+def _batch_learned(bn, torch, synth, nets, tabs, seed, args):
+    """The uneven batch with the learned proposal switched on for the largest network of
+    each size class (n in 10-19, 20-29, 30-39, 40-49, 50-60), each trained first on its
+    own chains' history, the others on the uniform swap in the shared fused launch; the
+    same batch all-uniform beside it.  ESS of the edge indicators (every 10th state) per
+    network; ESS/s = ESS over the whole batch's sampling time."""
+    ns = [d_.shape[1] for d_, *_ in nets]
+    pick = {}
+    for i, nn in enumerate(ns):
+        cls = min((nn - 10) // 10, 4)
+        if cls not in pick or nn > ns[pick[cls]]:
+            pick[cls] = i
+    chains, steps, thin, train = 32, args.batch_ess_steps, 10, args.batch_train
+    out = {"networks_learned": sorted(pick.values()), "n_learned": [ns[i] for i in sorted(pick.values())],
+           "chains_per_network": chains, "steps": steps}
+    for label in ("uniform", "learned"):
+        bat = bn.batch_create(tabs, chains, seed + 6, burn_in=train, record_every=thin,
+                              record_cap=(train + steps) // thin + 1)
+        nets_keep = []
+        if label == "learned":
+            for i in pick.values():
+                w = synth.mlp_init_weights(ns[i], 32, 512, seed + i)
+                net = bn.mlp_create(ns[i], w, hidden=512, d=32, batch_cap=chains, lr=2e-3)
+                nets_keep.append(net)
+                bn.chains_set_proposal(bat.chains(i), net, bn.PROPOSAL_TRAIN, eps_mix=0.1)
+                bn.chains_step(bat.chains(i), train)
+                bn.chains_set_proposal(bat.chains(i), net, bn.PROPOSAL_LEARNED, eps_mix=0.1)
+            others = [i for i in range(len(tabs)) if i not in pick.values()]
+            for i in others:                              # the same step count as the learned ones
+                bn.chains_step(bat.chains(i), train)
+        else:
+            bat.step(train)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bat.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1000.0
+        per = []
+        for i in sorted(pick.values()):
+            f = bn.chains_read(bat.chains(i), "edge_counts").sum(0) / (chains * steps)
+            ess = bn.chains_read(bat.chains(i), "ess")
+            unc = (f >= 0.05) & (f <= 0.95) & ~np.isnan(ess)
+            per.append(float(np.median(ess[unc])) if unc.any() else None)
+        out[label] = {"seconds": sec, "order_evals_per_s": len(tabs) * chains * steps / sec,
+                      "median_ess_of_learned_networks": per,
+                      "ess_per_s": [e / sec if e else None for e in per]}
+        bat.free()
+        for net in nets_keep:
+            net.free()
+    out["note"] = ("learned networks step through their own three-kernel path after the shared fused launch "
+                   "of the uniform networks (bn_batch_step); the all-uniform batch is the same networks, "
+                   "chains and seeds")
+    return out
+
+
+def _config_n20(bn, torch, synth, seed):
+    """20 ternary nodes, m = 1000, k = 4, with the pairwise prior (10 % of the true edges at
+    +1, 10 % of the non-edges at -1); 64 chains x 20,000 iterations through the one-shot
+    call, edge-posterior ESS from every 10th state."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t = bn.build_scores(data, arity, k, R=R)
+    bn.table_set_scan(t, bn.SCAN_PRUNED)
+    torch.cuda.synchronize()
+    prep = time.perf_counter() - t0
+    chains, iters = 64, 20000
+    bn.mcmc_run(t, chains, 2000, seed=seed + 20, burn_in=200)          # warm-up
+    out = bn.mcmc_run(t, chains, iters, seed=seed + 21, burn_in=iters // 10, thin=10)
+    st = out["stats"]
+    t.free()
+    return {"workload": "n20_k4_m1000 with the +-1 pairwise prior, 64 chains x 20,000 iterations",
+            "order_evals_per_s": chains * iters / (st["sample_ms"] / 1000.0), "sample_ms": st["sample_ms"],
+            "acceptance": st["acceptance"], "ess_median": st["ess_median"], "ess_min": st["ess_min"],
+            "uncertain_edges": st["uncertain_edges"],
+            "ess_per_s": st["ess_median"] / (st["sample_ms"] / 1000.0) if st["ess_median"] == st["ess_median"]
+            else None, "table_and_prune_s": prep, "best_score": out["best_score"]}
+
+
+def _config_n40(bn, torch, synth, seed, stream, flush, test_rate, hbm_peak):
+    """40 ternary nodes, m = 2000, k = 4 (3.69 M entries): 512 chains stepped by the
+    full-table scan, each step's three kernels replayed from a CUDA graph, on the tiling
+    the autotuner picks for 512 items per node; the same chains on the pruned table's
+    fused sampler beside it."""
+    data, arity, k, R, _ = synth.workload("n40_k4_m2000")
+    t = bn.build_scores(data, arity, k, R=R)
+    S = bn.table_info(t)["sets_per_node"]
+    n = data.shape[1]
+    chains = 512
+    sub, nchunk, tuned_us = bn.table_autotune(t, chains)
+    with torch.cuda.stream(stream):
+        ch = bn.chains_create(t, chains, seed + 40)
+        bn.chains_step(ch, 5, stream=stream.cuda_stream)
+        steps = 100
+        ms = _timed(bn, torch, ch, steps, stream, pieces=steps, flush=flush)
+        i0 = int(bn.chains_read(ch, "items")[0])
+        scan_ms, scan_l = bn.chains_step_profiled(ch, 50, stream=stream.cuda_stream)
+        items = int(bn.chains_read(ch, "items")[0]) - i0
+        ch.free()
+        tests = items * S / max(scan_l, 1)
+        avg = scan_ms / max(scan_l, 1)
+        bn.table_set_scan(t, bn.SCAN_PRUNED)
+        fch = bn.chains_create(t, chains, seed + 41)
+        bn.chains_step(fch, 1000, stream=stream.cuda_stream)
+        fms = _timed(bn, torch, fch, 4000, stream, pieces=4, flush=flush)
+        fch.free()
+    t.free()
+    return {"workload": "n40_k4_m2000, 512 chains", "full_table": {
+                "order_evals_per_s": chains * steps / (ms / 1000.0), "ms_per_step": ms / steps,
+                "tiling": {"stage_entries": sub, "blocks_per_node": nchunk, "tuned_us_per_launch": tuned_us},
+                "scan_avg_ms": avg, "tests_per_s": tests / (avg / 1000.0),
+                "test_frac": tests / (avg / 1000.0) / test_rate,
+                "hbm_frac_algorithmic": (4 * n * S + 8 * S) / (avg / 1000.0) / 1e9 / hbm_peak,
+                "note": "a step: predecessor lists + the scan + the MH update, replayed from a CUDA graph"},
+            "pruned_fused": {"order_evals_per_s": chains * 4000 / (fms / 1000.0), "us_per_iteration": 1000.0 * fms / 4000}}
+
+
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
@@ -348,19 +481,24 @@ def main():
     flush = (torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev),
              torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev))
     hbm_bytes = 4 * n * S + 8 * S            # sorted positions of every entry + the mask table once
-    for B in (1, 2, 4):
+    test_rate = bn.measure_test_rate()       # measured peak of the scan's consistency test
+    for B in SCORE_B:
         orders = torch.from_numpy(synth.random_orders(n, B, 100 + B)).to(dev)
         for _ in range(3):
             bn.score_orders_profiled(table, orders)
         times = []
-        for _ in range(10):
+        for _ in range(10 if B <= 64 else 5):
             _flush_l2(torch, flush, torch.cuda.current_stream())
             torch.cuda.synchronize()
             times.append(1000.0 * bn.score_orders_profiled(table, orders)[2])
         us = float(np.median(times))
-        hbm_leg.append({"orders": B, "scan_us": us, "scan_us_mean": float(np.mean(times)),
-                        "calls": len(times), "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
-                        "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak})
+        tests = float(n) * S * B                 # (entry, order) consistency tests of one pass
+        hbm_leg.append({"orders": B, "kernel": "k_scan_nodes" if n * B <= 256 else "k_scan",
+                        "scan_us": us, "scan_us_mean": float(np.mean(times)), "calls": len(times),
+                        "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
+                        "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak,
+                        "tests_per_s": tests / (us / 1e6), "test_frac": tests / (us / 1e6) / test_rate,
+                        "order_evals_per_s": B / (us / 1e6)})
 
     # ---- the sum-based order score of the prior scorer (Sec. III.B) on the same table:
     #      one order, whole-call device time, L2 flushed before every call ------------------
@@ -419,13 +557,29 @@ def main():
         clk = ClockSampler(local)
         clk.start()
         l0 = bn.kernel_launches()
+        it0 = int(bn.chains_read(chains, "items")[0])
         ms = _timed(bn, torch, chains, args.steps * ips, stream, pieces=args.steps, flush=flush)
         launches = bn.kernel_launches() - l0
+        items_head = int(bn.chains_read(chains, "items")[0]) - it0
         barrier()
         clocks = clk.stop()
         # the fused sampler kernel, launch by launch (up to 1024 iterations per launch)
         fused_ms, fused_l = bn.chains_step_profiled(chains, max(ips, 256) * 4, stream=stream.cuda_stream)
         chains.free()
+
+    # ---- bn_score_orders on the pruned table (only entries no subset matches or beats) -----
+    pruned_scoring = []
+    for B in (1, 64, 1024, 8192):
+        orders = torch.from_numpy(synth.random_orders(n, B, 300 + B)).to(dev)
+        for _ in range(3):
+            bn.score_orders_profiled(table, orders)
+        times = []
+        for _ in range(10):
+            _flush_l2(torch, flush, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            times.append(1000.0 * bn.score_orders_profiled(table, orders)[2])
+        us = float(np.median(times))
+        pruned_scoring.append({"orders": B, "scan_us": us, "order_evals_per_s": B / (us / 1e6)})
 
     t_max = ms
     if world > 1:
@@ -490,9 +644,16 @@ def main():
                  "note": "uniform-swap chains of every network in one fused launch per 1024 steps "
                          "(bn_batch_step); the learned proposal runs per network (bn_chains_set_proposal)"}
         bat.free()
+        batch["learned_per_size_class"] = _batch_learned(bn, torch, synth, nets, tabs, seed, args)
         for tb in tabs:
             tb.free()
         del tabs
+
+    # ---- the other configurations of the metric's workload family ---------------------------
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = {"n20_64chains": _config_n20(bn, torch, synth, seed),
+                   "n40_512chains": _config_n40(bn, torch, synth, seed, stream, flush, test_rate, hbm_peak)}
 
     # ---- accuracy study (Sec. VI): ROC points with the prior schedule, noise tolerance ----
     accuracy = _accuracy(bn, synth, 29) if (rank == 0 and not args.no_accuracy) else None
@@ -514,30 +675,52 @@ def main():
 
     if rank == 0:
         clock_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        avg_fused = fused_ms / max(fused_l, 1)
+        iters_fused = max(ips, 256) * 4 / max(fused_l, 1)              # MH iterations per profiled launch
+        inst = FUSED_INST_PER_CHAIN_STEP * args.chains * iters_fused   # warp instructions per launch
+        issue_peak = n_sm * ISSUE_PER_SM * clock_mhz * 1e6
+        roof_head = {"kernel": "k_chain_fused<1> (the timed step: pruned table, one warp per chain, up to 1,024 "
+                               "MH iterations per launch)",
+                     "bound": "alu", "unit": "warp instructions/s",
+                     "achieved": inst / (avg_fused / 1000.0), "peak": issue_peak,
+                     "frac": inst / (avg_fused / 1000.0) / issue_peak, "traffic": None,
+                     "peak_source": f"derived: {n_sm} SMs x {ISSUE_PER_SM} schedulers x 1 warp instruction per "
+                                    f"clock x {clock_mhz:.0f} MHz (SM clock sampled in the timed region)",
+                     "per_launch": {"avg_ms": avg_fused, "launches": fused_l, "iterations": iters_fused,
+                                    "warp_instructions": inst,
+                                    "warp_instructions_per_chain_iteration": FUSED_INST_PER_CHAIN_STEP,
+                                    "us_per_iteration": 1000.0 * avg_fused / iters_fused},
+                     "note": "latency-bound: 256 chains are 256 warps on 152 SMs, and each warp's MH step is a "
+                             "chain of dependent shared-memory loads, shuffles and votes, so issue slots stay "
+                             "idle; the instruction count per chain-iteration is ncu's smsp__inst_executed.sum "
+                             "for this kernel at this workload; DRAM traffic is the survivors' and chains' "
+                             "state only (the table stays in shared memory)"}
         avg_full = scan_ms_full / max(scan_l_full, 1)
         tests = items_prof * S / max(scan_l_full, 1)                 # (entry, item) tests per launch
-        alu_peak = n_sm * ALU_LANES_PER_SM * clock_mhz * 1e6 / 1e9     # Gop/s
-        alu_ach = SCAN_ALU_OPS * tests / (avg_full / 1000.0) / 1e9
-        roof_full = {"kernel": "k_scan (full table)", "bound": "alu", "achieved": alu_ach, "peak": alu_peak,
-                     "unit": "Gop/s", "frac": alu_ach / alu_peak, "traffic": None,
-                     "peak_source": f"derived: {n_sm} SMs x {ALU_LANES_PER_SM} int32 logic/min lanes x "
-                                    f"{clock_mhz:.0f} MHz (measured SM clock)",
-                     "per_launch": {"tests": tests, "alu_ops_per_test": SCAN_ALU_OPS, "avg_ms": avg_full,
-                                    "launches": scan_l_full,
-                                    "hbm_bytes_algorithmic": 12 * n * S,
-                                    "hbm_frac_of_measured": 12 * n * S / (avg_full / 1000.0) / 1e9 / hbm_peak},
+        roof_scan = {"kernel": "k_scan<1024,0> (full table, one launch per sampler step of all chains)",
+                     "bound": "alu", "unit": "tests/s", "achieved": tests / (avg_full / 1000.0),
+                     "peak": test_rate, "frac": tests / (avg_full / 1000.0) / test_rate,
+                     "traffic": SCAN_TRAFFIC_BYTES,
+                     "peak_source": "measured in this run: bn_measure_test_rate (the scan's exact consistency "
+                                    "test on register operands, 8 x 256 threads per SM, CUDA events)",
+                     "per_launch": {"tests": tests, "avg_ms": avg_full, "launches": scan_l_full,
+                                    "hbm_bytes_algorithmic": 4 * n * S + 8 * S,
+                                    "hbm_frac_of_measured": (4 * n * S + 8 * S) / (avg_full / 1000.0) / 1e9 / hbm_peak},
                      "share_of_step": avg_full / (ms_full / args.steps),
-                     "note": "the paper's scan (a6) over the full table for a step of all chains' orders, timed "
-                             "in this run (full_scan); the headline step runs the pruned fused sampler "
-                             "k_chain_fused instead, which is latency-bound (one warp per chain, under two "
-                             "warps per SM; see pruned_step)"}
-        avg_fused = fused_ms / max(fused_l, 1)
-        cpu = None
+                     "note": "the paper's scan (a6) over the full table for a step of all chains' orders "
+                             "(full_scan): the table is read once per 256 orders, so the consistency tests, "
+                             "not HBM, bound it; traffic = ncu dram bytes read + written per launch"}
+        cpu = cpu1 = None
         if world == 1 and not args.no_cpu_baseline:
-            rate, done, el = oracle_sample(args.cpu_seconds)
-            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{done} order evaluations ({el:.1f} s) of the oracle's MH sampler at n=60, k=4, "
-                             "full order score per iteration, on a seeded stand-in table of the workload's shape"}
+            nt = os.cpu_count() or 1
+            rate, done, el, used = oracle_sample(args.cpu_seconds, threads=nt)
+            cpu = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                   "sample": f"{done} order evaluations ({el:.1f} s) of the oracle's MH sampler at n=60, k=4 "
+                             f"(full order score per iteration), {used} chains at a time in {used} host threads "
+                             f"of the {nt} cores, on a seeded stand-in table of the workload's shape"}
+            rate1, done1, el1, _ = oracle_sample(args.cpu_seconds / 2, threads=1)
+            cpu1 = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"{done1} order evaluations ({el1:.1f} s), one thread"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -548,11 +731,24 @@ def main():
                     "note": f"per call: bn_build_scores from host data + pruning + bn_mcmc_run of {e2e_steps} "
                             f"steps x {args.chains} chains + results to host"},
             "gpu_launches": int(launches),
-            "roofline": roof_full,
-            "roofline_hbm": {"kernel": "k_scan_nodes (bn_score_orders, full table, a few orders)", "bound": "hbm",
+            "work_per_iteration": {"order_evals": args.chains,
+                                   "nodes_rescored": items_head / (args.steps * ips),
+                                   "survivors_per_node_mean": float(survivors.mean()),
+                                   "note": "every iteration scores a full order of each chain; only the nodes "
+                                           "between the swapped positions are re-scored (the others keep their "
+                                           "parent sets), each over its surviving entries in score order"},
+            "roofline": roof_head,
+            "roofline_scan": roof_scan,
+            "roofline_hbm": {"kernel": "k_scan_nodes (bn_score_orders, full table, one order)", "bound": "hbm",
                              "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_leg[0]["frac"], "traffic": None, "peak_source": peak_src,
-                             "bytes_algorithmic": hbm_bytes, "by_orders": hbm_leg},
+                             "bytes_algorithmic": hbm_bytes},
+            "score_orders": {"by_orders": hbm_leg, "test_rate_peak": test_rate, "pruned_table": pruned_scoring,
+                             "note": "bn_score_orders on B random orders of the full n=60 table: scan kernel time "
+                                     "(CUDA events around its launch, L2 flushed before every call); HBM fraction "
+                                     "on 4 B per (node, entry) + 8 B per entry, test fraction of the measured "
+                                     "consistency-test peak; pruned_table: the same call once the table keeps "
+                                     "only the entries no subset matches or beats (identical results)"},
             "pruned_step": {"kernel": "k_chain_fused (up to 1024 MH iterations per launch, one warp per chain)",
                             "avg_ms_per_launch": avg_fused, "launches": fused_l,
                             "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
@@ -569,7 +765,9 @@ def main():
             "sum_score": sum_score,
             "uneven_batch": batch,
             "accuracy": accuracy,
+            "configs": configs,
             "cpu_baseline": cpu,
+            "cpu_baseline_1core": cpu1,
             "clocks": clocks,
             "table_build_s": build_s,
             "table_entries_per_s": n * S / build_s,

@@ -79,6 +79,18 @@ int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int
                     const double* R, const bn_score_params* params, int mem,
                     void* stream, bn_table** out);
 
+/* bn_build_scores for `count` networks of uneven size in one call (many-network batches,
+ * the paper learns one network at a time): network i has data[i] (m[i] x n[i]), arity[i],
+ * k[i], R[i] (R may be NULL, or R[i] NULL: no prior) and params[i] (params may be NULL:
+ * K2).  The host checks every network first; the builds then run concurrently on a few
+ * internal streams that fork from and join into `stream`.  Each table equals the one
+ * bn_build_scores builds from the same arguments, entry for entry.  out: count table
+ * pointers (all NULL on error).  Errors: as bn_build_scores, the message naming the
+ * network. */
+int bn_build_scores_batch(int count, const uint8_t* const* data, const int* m, const int* n,
+                          const uint8_t* const* arity, const int* k, const double* const* R,
+                          const bn_score_params* params, int mem, void* stream, bn_table** out);
+
 /* Wrap an existing table of scores (n x S(n-1,k) float64, node-major, rank order; the
  * layout bn_table_scores returns).  Used to score orders against an externally built
  * table.  Errors: BN_EINVAL (NaN or +inf scores, sizes), BN_ENOMEM, BN_ECUDA. */
@@ -181,6 +193,11 @@ int bn_table_pruned(const bn_table* t, int64_t* survivors_per_node);
  * {512, 1024, 2048} entries) x (blocks per SM target in {1, 2, 4, 8, 16}) tiling on this
  * table with synthetic work lists of max_items (node, order) items per node, and keeps
  * the fastest for later scans of up to that many items (per 256-item group, up to 2048).
+ * It also runs by itself: the first bn_score_orders call that takes the full-table scan
+ * and the first bn_chains_create on a table not in BN_SCAN_PRUNED mode tune the tiling
+ * for their number of 256-item groups (tens of milliseconds once per table and group
+ * count; BN_AUTOTUNE=0 in the environment keeps the fixed tiling).  Results do not depend
+ * on the tiling.
  * chosen (3 int64, may be NULL): stage size, blocks per node, microseconds per launch.
  * The table's scan mode is unchanged.  Errors: BN_EINVAL, BN_EUNSUPPORTED, BN_ECUDA. */
 int bn_table_autotune(bn_table* t, int max_items, void* stream, int64_t* chosen);
@@ -215,6 +232,18 @@ typedef struct {
     int      record_cap;  /* max recorded states per chain (ESS series length)          */
     int      trace;       /* 1: keep per-step score and accept flag (chains x steps cap) */
     int64_t  trace_cap;   /* steps of trace kept per chain                              */
+    /* bn_mcmc_run only (bn_chains_create and bn_batch_create ignore these):           */
+    int      proposal;    /* BN_PROPOSAL_UNIFORM (0, the paper's swap) or
+                             BN_PROPOSAL_LEARNED (1): train_iters uniform steps that train
+                             the network (BN_PROPOSAL_TRAIN), then the sampling steps with
+                             the learned proposal                                        */
+    double   eps_mix;     /* learned: weight of the uniform component, in (0, 1]         */
+    int64_t  train_iters; /* learned: training steps before the sampling steps           */
+    int      thin;        /* > 0: record every thin-th post-burn-in state and fill the
+                             ESS fields of bn_mcmc_stats; 0: no ESS                       */
+    struct bn_mlp* net;   /* learned: the proposal network (its n, batch_cap >= chains);
+                             NULL: the call creates one (d = 32, H = 512, Adam lr 2e-3,
+                             weights drawn from seed) and frees it                        */
 } bn_mcmc_params;
 
 /* Create chains over a table.  init_orders: chains x n (NULL = Philox initial orders,
@@ -270,15 +299,35 @@ int bn_chains_read(const bn_chains* c, int what, void* out, int mem, void* strea
 
 void bn_chains_free(bn_chains* c);
 
-/* One-shot run (Algorithm 1): chains from Philox initial orders, `steps` steps, then
+/* Summary of a bn_mcmc_run (the edge-posterior ESS of the benchmark spec's metric):
+ * acceptance over the sampling steps; per directed edge m -> i the Geyer initial-
+ * monotone-sequence ESS of its indicator series (every thin-th post-burn-in state),
+ * summed over the chains in which the series is not constant; median and minimum over
+ * the uncertain edges, those with frequency 0.05 <= f <= 0.95 and a defined ESS. */
+typedef struct {
+    double  acceptance;      /* accepted / proposed over the sampling steps, all chains   */
+    double  ess_median;      /* NaN when thin == 0 or no edge is uncertain                */
+    double  ess_min;
+    int64_t uncertain_edges;
+    double  sample_ms;       /* device time of the sampling steps (CUDA events)           */
+    double  train_ms;        /* device time of the training steps (0 for uniform)         */
+    int64_t order_evals;     /* chains x (train_iters + steps): every step scores a full order */
+} bn_mcmc_stats;
+
+/* One-shot run (Algorithm 1): chains from Philox initial orders; with the learned
+ * proposal first p->train_iters training steps, then `steps` sampling steps; edge counts
+ * from step p->burn_in on (counted over both phases); then
  *   best_order  n uint8       the best order over all chains
  *   best_dag    n x n uint8   its greedy DAG, best_dag[i*n + m] = 1 iff m -> i
  *   best_score  1 float64
  *   edge_freq   n x n float64 fraction of post-burn-in steps (all chains) with m -> i
- * Any output may be NULL.  Outputs are host memory. */
+ *   stats       the summary above
+ * Any output may be NULL.  Outputs are host memory.  p->trace and the record fields are
+ * ignored (thin sets the recording).  Errors: BN_EINVAL (proposal, eps_mix, a network of
+ * the wrong size), BN_ENOMEM, BN_ETIMEOUT, BN_ECUDA. */
 int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
                 uint8_t* best_order, uint8_t* best_dag, double* best_score,
-                double* edge_freq, void* stream);
+                double* edge_freq, bn_mcmc_stats* stats, void* stream);
 
 /* Batches of networks of uneven size (the paper samples one network at a time): count
  * networks, each with its own table and chain parameters.  bn_batch_step advances every
@@ -388,6 +437,16 @@ int bn_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int M, int N, i
  * status word.  Returns BN_ETIMEOUT when both waits ran out as intended (the context
  * stays usable), BN_ECUDA otherwise. */
 int bn_selftest_timeout(int64_t timeout_ns, void* stream);
+
+/* Measured peak rate of the scan's consistency test on this GPU (the paper has no
+ * counterpart; it is the denominator of the full-table scan's roofline): a kernel that
+ * runs the scan's own inner loop -- per two entries one 8-byte load of their sorted
+ * positions and one 16-byte load of their masks from shared memory, then per entry two
+ * three-input logic ops folding the 64-bit AND-NOT, a zero test and a predicated
+ * unsigned min -- over 1,024 entries resident in shared memory (no HBM, no staging),
+ * 8 blocks of 256 threads per SM, timed by CUDA events on `stream` (best of three
+ * launches after one warm-up).  *tests_per_s receives (tests per launch) / (time). */
+int bn_measure_test_rate(void* stream, double* tests_per_s);
 
 const char* bn_last_error(void);     /* thread-local; "" when no error                 */
 const char* bn_version(void);

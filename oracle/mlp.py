@@ -98,9 +98,13 @@ def mlp_log_q(logits, eps):
     return np.log((1.0 - eps) * np.exp(logits - lse) + eps / P)
 
 
-def mlp_loss_grad(prm: MLPParams, orders, pairs, alpha, rounded=True):
+def mlp_loss_grad(prm: MLPParams, orders, pairs, alpha, rounded=True, with_terms=False):
     """Mean BCE of sigmoid(logit[pair]) against alpha, and its gradient with respect to
-    every parameter (dict with the same names)."""
+    every parameter (dict with the same names).  with_terms: also the per-example
+    factors every gradient sums over the batch, as grads["terms"]: the input x and the
+    activations h1, h2, d loss / d logit[pair] ("dl"), the backward GEMM inputs dz2, dz1,
+    the input gradient dx (B x n d, whose slices the embedding gradient sums), the
+    pre-activations z1, z2 and the rounded weights W1, W2 they were computed with."""
     f = mlp_forward(prm, orders, rounded)
     B = f["x"].shape[0]
     rows = np.arange(B)
@@ -126,7 +130,11 @@ def mlp_loss_grad(prm: MLPParams, orders, pairs, alpha, rounded=True):
     d = prm.E.shape[1]
     dE = np.zeros_like(prm.E)
     np.add.at(dE, np.asarray(orders, np.int64).reshape(-1), dx.reshape(-1, d))
-    return loss, dict(E=dE, W1=dW1, b1=db1, W2=dW2, b2=db2, W3=dW3, b3=db3)
+    grads = dict(E=dE, W1=dW1, b1=db1, W2=dW2, b2=db2, W3=dW3, b3=db3)
+    if with_terms:
+        grads["terms"] = dict(x=f["x"], h1=f["h1"], h2=f["h2"], dl=dl, dz2=dz2, dz1=dz1, dx=dx,
+                              z1=f["z1"], z2=f["z2"], W1=f["W1"], W2=f["W2"], dh2=dh2, dh1=dh1)
+    return loss, grads
 
 
 def adam_step(prm: MLPParams, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -45,7 +45,15 @@ class ScoreParams(C.Structure):
 class MCMCParams(C.Structure):
     _fields_ = [("chains", C.c_int), ("burn_in", C.c_int64), ("seed", C.c_uint64),
                 ("literal_log", C.c_int), ("record_every", C.c_int), ("record_cap", C.c_int),
-                ("trace", C.c_int), ("trace_cap", C.c_int64)]
+                ("trace", C.c_int), ("trace_cap", C.c_int64),
+                ("proposal", C.c_int), ("eps_mix", C.c_double), ("train_iters", C.c_int64),
+                ("thin", C.c_int), ("net", C.c_void_p)]
+
+
+class MCMCStats(C.Structure):
+    _fields_ = [("acceptance", C.c_double), ("ess_median", C.c_double), ("ess_min", C.c_double),
+                ("uncertain_edges", C.c_int64), ("sample_ms", C.c_double), ("train_ms", C.c_double),
+                ("order_evals", C.c_int64)]
 
 
 class MLPParams(C.Structure):
@@ -70,6 +78,7 @@ def _load():
     _L.bn_build_scores.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, C.POINTER(ScoreParams),
                                    C.c_int, _vp, C.POINTER(_vp)]
     _L.bn_table_from_scores.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_build_scores_batch.argtypes = [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp, _vp]
     _L.bn_table_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]
     _L.bn_table_scores.argtypes = [_vp, C.c_int, _vp, C.c_int, _vp]
@@ -88,7 +97,9 @@ def _load():
     _L.bn_chains_read.argtypes = [_vp, C.c_int, _vp, C.c_int, _vp]
     _L.bn_chains_free.argtypes = [_vp]
     _L.bn_chains_free.restype = None
-    _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp, _vp]
+    _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp,
+                               C.POINTER(MCMCStats), _vp]
+    _L.bn_measure_test_rate.argtypes = [_vp, C.POINTER(C.c_double)]
     _L.bn_mlp_create.argtypes = [C.c_int, C.POINTER(MLPParams)] + [_vp] * 7 + [C.c_int, _vp, C.POINTER(_vp)]
     _L.bn_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, _vp]
     _L.bn_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_int, _vp]
@@ -222,6 +233,28 @@ def build_scores(data, arity, k, R=None, score_kind=0, ess=1.0, log10_gamma=0.0)
     return Table(h)
 
 
+def build_scores_batch(nets, score_kind=0, ess=1.0, log10_gamma=0.0):
+    """bn_build_scores_batch: one table per (data, arity, k, R) of ``nets`` (R may be None),
+    host arrays, built concurrently."""
+    cnt = len(nets)
+    keep = []
+    dps, aps, rps = (C.c_void_p * cnt)(), (C.c_void_p * cnt)(), (C.c_void_p * cnt)()
+    ms, ns, ks = (C.c_int * cnt)(), (C.c_int * cnt)(), (C.c_int * cnt)()
+    for i, (data, arity, k, R) in enumerate(nets):
+        d = _host(data, np.uint8)
+        a = _host(arity, np.uint8)
+        r = _host(R, np.float64) if R is not None else None
+        keep += [d, a, r]
+        dps[i] = d.ctypes.data
+        aps[i] = a.ctypes.data
+        rps[i] = r.ctypes.data if r is not None else None
+        ms[i], ns[i], ks[i] = d.shape[0], d.shape[1], int(k)
+    prm = (ScoreParams * cnt)(*[ScoreParams(score_kind, ess, log10_gamma) for _ in range(cnt)])
+    out = (C.c_void_p * cnt)()
+    _check(lib().bn_build_scores_batch(cnt, dps, ms, ns, aps, ks, rps, prm, MEM_HOST, None, out))
+    return [Table(C.c_void_p(out[i])) for i in range(cnt)]
+
+
 def table_from_scores(scores, k) -> Table:
     h = _vp()
     if _is_cuda(scores):
@@ -331,6 +364,14 @@ def table_pruned(t: Table):
     return out
 
 
+def measure_test_rate(stream=None) -> float:
+    """Measured peak of the scan's consistency test on this GPU, tests per second
+    (bn_measure_test_rate)."""
+    r = C.c_double()
+    _check(lib().bn_measure_test_rate(stream, C.byref(r)))
+    return r.value
+
+
 def unrank(N, k, rank) -> int:
     m = C.c_uint64()
     _check(lib().bn_unrank(N, k, rank, C.byref(m)))
@@ -373,7 +414,7 @@ def chains_create(t: Table, chains, seed, burn_in=0, init_orders=None, literal_l
                   record_every=0, record_cap=0, trace_cap=0) -> Chains:
     n = table_info(t)["n"]
     p = MCMCParams(chains, burn_in, seed, 1 if literal_log else 0, record_every, record_cap,
-                   1 if trace_cap else 0, trace_cap)
+                   1 if trace_cap else 0, trace_cap, 0, 0.0, 0, 0, None)
     h = _vp()
     io = _host(init_orders, np.uint8) if init_orders is not None else None
     _check(lib().bn_chains_create(t.handle, C.byref(p), _ptr(io), MEM_HOST, None, C.byref(h)))
@@ -412,17 +453,24 @@ def chains_read(c: Chains, what: str):
     return out
 
 
-def mcmc_run(t: Table, chains, steps, seed, burn_in=0, literal_log=False):
-    """Algorithm 1 end to end (bn_mcmc_run): best order, its greedy DAG, best score and
-    edge frequencies."""
+def mcmc_run(t: Table, chains, steps, seed, burn_in=0, literal_log=False, proposal=0, eps_mix=0.1,
+             train_iters=0, thin=0, net=None):
+    """Algorithm 1 end to end (bn_mcmc_run): best order, its greedy DAG, best score, edge
+    frequencies and the run's summary (acceptance, edge-posterior ESS when thin > 0,
+    device times).  proposal = PROPOSAL_LEARNED trains the network (given, or one the
+    call creates) for train_iters steps first."""
     n = table_info(t)["n"]
-    p = MCMCParams(chains, burn_in, seed, 1 if literal_log else 0, 0, 0, 0, 0)
+    p = MCMCParams(chains, burn_in, seed, 1 if literal_log else 0, 0, 0, 0, 0,
+                   proposal, eps_mix, train_iters, thin, net.handle if net is not None else None)
     bo = np.empty(n, np.uint8)
     dag = np.empty((n, n), np.uint8)
     bs = np.empty(1, np.float64)
     ef = np.empty((n, n), np.float64)
-    _check(lib().bn_mcmc_run(t.handle, C.byref(p), steps, _ptr(bo), _ptr(dag), _ptr(bs), _ptr(ef), None))
-    return dict(best_order=bo, best_dag=dag, best_score=float(bs[0]), edge_freq=ef)
+    st = MCMCStats()
+    _check(lib().bn_mcmc_run(t.handle, C.byref(p), steps, _ptr(bo), _ptr(dag), _ptr(bs), _ptr(ef), C.byref(st),
+                             None))
+    stats = {f: getattr(st, f) for f, _ in MCMCStats._fields_}
+    return dict(best_order=bo, best_dag=dag, best_score=float(bs[0]), edge_freq=ef, stats=stats)
 
 
 # ---- learned proposal ----------------------------------------------------------------

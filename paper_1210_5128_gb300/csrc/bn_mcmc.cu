@@ -1256,6 +1256,10 @@ extern "C" int bn_chains_create(const bn_table* t, const bn_mcmc_params* p, cons
         return set_error(BN_EINVAL, "bn_chains_create: negative burn_in/record/trace");
     if (mem != BN_MEM_HOST && mem != BN_MEM_DEVICE) return set_error(BN_EINVAL, "bn_chains_create: bad mem");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->chains <= 2048) {                          // the full-table scan's tiling, once per table
+        int rt = ensure_tuned(t, p->chains, s);
+        if (rt) return rt;
+    }
     bn_chains* ch = new bn_chains();
     ch->t = t;
     ch->p = *p;
@@ -1623,21 +1627,91 @@ extern "C" int bn_chains_set_proposal(bn_chains* ch, bn_mlp* m, int mode, double
     return BN_OK;
 }
 
+// seeded initial weights of the proposal network bn_mcmc_run creates when none is given:
+// uniform in [-1, 1) (fan-in scaled for the dense layers) from splitmix64, zero biases
+static void default_mlp_weights(int n, int d, int H, uint64_t seed, std::vector<float>* w)
+{
+    const int P = n * (n - 1) / 2;
+    uint64_t x = seed ^ 0x6a09e667f3bcc909ull;
+    auto next = [&]() {
+        uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+    };
+    const size_t sz[7] = {(size_t)n * d, (size_t)H * n * d, (size_t)H, (size_t)H * H, (size_t)H, (size_t)P * H, (size_t)P};
+    const float scale[7] = {1.f, 1.f / std::sqrt((float)(n * d)), 0.f, 1.f / std::sqrt((float)H), 0.f,
+                            1.f / std::sqrt((float)H), 0.f};
+    for (int i = 0; i < 7; ++i) {
+        w[i].resize(sz[i]);
+        for (size_t j = 0; j < sz[i]; ++j) w[i][j] = scale[i] == 0.f ? 0.f : next() * scale[i];
+    }
+}
+
 extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,
-                           uint8_t* best_dag, double* best_score, double* edge_freq, void* stream)
+                           uint8_t* best_dag, double* best_score, double* edge_freq, bn_mcmc_stats* stats,
+                           void* stream)
 {
     set_error(BN_OK, "");
     if (!t || !p || steps < 0) return set_error(BN_EINVAL, "bn_mcmc_run: bad arguments");
+    const bool learned = p->proposal == BN_PROPOSAL_LEARNED;
+    if (!learned && p->proposal != BN_PROPOSAL_UNIFORM)
+        return set_error(BN_EINVAL, "bn_mcmc_run: proposal %d (BN_PROPOSAL_UNIFORM or BN_PROPOSAL_LEARNED)",
+                         p->proposal);
+    if (learned && (!(p->eps_mix > 0.0 && p->eps_mix <= 1.0) || p->train_iters < 0))
+        return set_error(BN_EINVAL, "bn_mcmc_run: eps_mix in (0, 1] and train_iters >= 0 for the learned proposal");
+    if (p->thin < 0) return set_error(BN_EINVAL, "bn_mcmc_run: thin=%d", p->thin);
+    if (learned && p->net && (p->net->n != t->n || p->net->cap < p->chains))
+        return set_error(BN_EINVAL, "bn_mcmc_run: the network's n or batch_cap does not fit the run");
     cudaStream_t s = (cudaStream_t)stream;
+    const int n = t->n, C = p->chains;
+    const int64_t train = learned ? p->train_iters : 0, total = train + steps;
+    bn_mcmc_params cp = *p;
+    cp.trace = 0;
+    cp.trace_cap = 0;
+    cp.record_every = p->thin;
+    cp.record_cap = p->thin > 0 ? (int)std::max<int64_t>(1, (total - p->burn_in + p->thin - 1) / p->thin) : 0;
     bn_chains* ch = nullptr;
-    int rc = bn_chains_create(t, p, nullptr, BN_MEM_HOST, stream, &ch);
+    int rc = bn_chains_create(t, &cp, nullptr, BN_MEM_HOST, stream, &ch);
     if (rc) return rc;
+    bn_mlp* own = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     struct G {
         bn_chains* c;
-        ~G() { bn_chains_free(c); }
-    } g{ch};
+        bn_mlp** m;
+        cudaEvent_t* e;
+        ~G()
+        {
+            bn_chains_free(c);
+            bn_mlp_free(*m);
+            for (int i = 0; i < 3; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } g{ch, &own, ev};
+    for (int i = 0; i < 3; ++i) BN_CUDA(cudaEventCreate(&ev[i]));
+    bn_mlp* net = p->net;
+    if (learned && !net) {
+        const int d = 32, H = 512;
+        std::vector<float> w[7];
+        default_mlp_weights(n, d, H, p->seed, w);
+        bn_mlp_params mp = {d, H, C, 2e-3f, 0.f, 0.f, 0.f};
+        if ((rc = bn_mlp_create(n, &mp, w[0].data(), w[1].data(), w[2].data(), w[3].data(), w[4].data(),
+                                w[5].data(), w[6].data(), BN_MEM_HOST, stream, &own)))
+            return rc;
+        net = own;
+    }
+    BN_CUDA(cudaEventRecord(ev[0], s));
+    if (learned) {
+        if ((rc = bn_chains_set_proposal(ch, net, BN_PROPOSAL_TRAIN, p->eps_mix, stream))) return rc;
+        if ((rc = bn_chains_step(ch, train, stream))) return rc;
+        if ((rc = bn_chains_set_proposal(ch, net, BN_PROPOSAL_LEARNED, p->eps_mix, stream))) return rc;
+    }
+    std::vector<int64_t> acc0(C), acc1(C);
+    if (stats) BN_CUDA(cudaMemcpyAsync(acc0.data(), ch->S.accepts, 8 * (size_t)C, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaEventRecord(ev[1], s));
     if ((rc = bn_chains_step(ch, steps, stream))) return rc;
-    const int n = t->n, C = p->chains;
+    BN_CUDA(cudaEventRecord(ev[2], s));
     uint8_t *d_o = nullptr, *d_dag = nullptr;
     double *d_s = nullptr, *d_f = nullptr;
     BN_CUDA(cudaMallocAsync((void**)&d_o, n, s));
@@ -1646,18 +1720,50 @@ extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t s
     BN_CUDA(cudaMallocAsync((void**)&d_f, 8 * (size_t)n * n, s));
     k_pick_best<<<1, 64, 0, s>>>(ch->S.best_score, ch->S.best_order, ch->S.best_rank, t->pst, C, n, d_o, d_dag, d_s);
     BN_LAUNCH_CHECK("k_pick_best");
-    const double denom = (double)C * (double)std::max<int64_t>(0, steps - p->burn_in);
+    const double denom = (double)C * (double)std::max<int64_t>(0, total - p->burn_in);
     k_edge_freq<<<(n * n + 127) / 128, 128, 0, s>>>(ch->S.edge, C, n, denom, d_f);
     BN_LAUNCH_CHECK("k_edge_freq");
+    std::vector<double> f((size_t)n * n);
     if (best_order) BN_CUDA(cudaMemcpyAsync(best_order, d_o, n, cudaMemcpyDeviceToHost, s));
     if (best_dag) BN_CUDA(cudaMemcpyAsync(best_dag, d_dag, (size_t)n * n, cudaMemcpyDeviceToHost, s));
     if (best_score) BN_CUDA(cudaMemcpyAsync(best_score, d_s, 8, cudaMemcpyDeviceToHost, s));
-    if (edge_freq) BN_CUDA(cudaMemcpyAsync(edge_freq, d_f, 8 * (size_t)n * n, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaMemcpyAsync(f.data(), d_f, 8 * (size_t)n * n, cudaMemcpyDeviceToHost, s));
+    if (stats) BN_CUDA(cudaMemcpyAsync(acc1.data(), ch->S.accepts, 8 * (size_t)C, cudaMemcpyDeviceToHost, s));
     cudaFreeAsync(d_o, s);
     cudaFreeAsync(d_dag, s);
     cudaFreeAsync(d_s, s);
     cudaFreeAsync(d_f, s);
     BN_CUDA(cudaStreamSynchronize(s));
+    if (edge_freq) std::copy(f.begin(), f.end(), edge_freq);
+    if (stats) {
+        bn_mcmc_stats st;
+        int64_t acc = 0;
+        for (int c = 0; c < C; ++c) acc += acc1[c] - acc0[c];
+        st.acceptance = steps > 0 ? (double)acc / ((double)C * (double)steps) : 0.0;
+        float ms = 0.f;
+        BN_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        st.train_ms = learned ? ms : 0.0;
+        BN_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+        st.sample_ms = ms;
+        st.order_evals = (int64_t)C * total;
+        st.ess_median = st.ess_min = std::nan("");
+        st.uncertain_edges = 0;
+        if (p->thin > 0) {
+            std::vector<double> ess((size_t)n * n);
+            if ((rc = bn_chains_read(ch, BN_OUT_ESS, ess.data(), BN_MEM_HOST, stream))) return rc;
+            std::vector<double> unc;
+            for (size_t e = 0; e < ess.size(); ++e)
+                if (f[e] >= 0.05 && f[e] <= 0.95 && !std::isnan(ess[e])) unc.push_back(ess[e]);
+            if (!unc.empty()) {
+                std::sort(unc.begin(), unc.end());
+                const size_t h = unc.size() / 2;
+                st.ess_median = unc.size() % 2 ? unc[h] : 0.5 * (unc[h - 1] + unc[h]);
+                st.ess_min = unc[0];
+                st.uncertain_edges = (int64_t)unc.size();
+            }
+        }
+        *stats = st;
+    }
     return BN_OK;
 }
 

@@ -518,6 +518,55 @@ __global__ void k_reduce_orders(const uint32_t* __restrict__ list_best, const ui
     }
 }
 
+// the full-table scan's tiling for up to max_items items per node, tuned on first use: the
+// first scan with a new number of 256-item groups (<= 8) times every tiling the autotuner
+// knows on this table (tens of milliseconds once) and keeps the fastest.  BN_AUTOTUNE=0 in
+// the environment keeps the fixed plan.
+int ensure_tuned(const bn_table* t, int max_items, cudaStream_t s)
+{
+    if (!t || t->scan_mode == BN_SCAN_PRUNED || max_items < 1) return BN_OK;
+    const int groups = (max_items + SCAN_THREADS - 1) / SCAN_THREADS;
+    if (groups > 8 || t->tuned_sub[groups]) return BN_OK;
+    static const bool off = [] {
+        const char* e = getenv("BN_AUTOTUNE");
+        return e && e[0] == '0';
+    }();
+    if (off) return BN_OK;
+    return bn_table_autotune(const_cast<bn_table*>(t), groups * SCAN_THREADS, s, nullptr);
+}
+
+// The peak rate of the scan's consistency test on this GPU, for its roofline: the scan's
+// own inner loop (two entries per step: their sorted positions by one 8-byte and their
+// masks by one 16-byte shared-memory load, then two test_min) over 1,024 entries that
+// stay in shared memory, so nothing waits on HBM or on the staging barriers.  The loads
+// stay inside the loop (1,024 entries do not fit in registers).
+static constexpr int TEST_RATE_ENTRIES = 1024;
+
+__global__ void __launch_bounds__(256) k_test_rate(uint32_t iters, uint32_t salt, uint32_t* sink)
+{
+    __shared__ uint2 s_p[TEST_RATE_ENTRIES / 2];
+    __shared__ uint4 s_m[TEST_RATE_ENTRIES / 2];
+    for (int j = threadIdx.x; j < TEST_RATE_ENTRIES / 2; j += blockDim.x) {
+        const uint32_t h = (uint32_t)j * 0x9e3779b9u ^ salt;
+        s_p[j] = make_uint2(h >> 1, (h * 0x85ebca6bu) >> 1);
+        s_m[j] = make_uint4(h & 0x0f0f0f0fu, h & 0x00ff00ffu, (h * 3u) & 0x0f0f0f0fu, (h * 5u) & 0x00ff00ffu);
+    }
+    __syncthreads();
+    const uint32_t x = (threadIdx.x + blockIdx.x * 256u) * 0x27d4eb2du;
+    const uint32_t nlo = ~(x & 0xf0f0f0f0u), nhi = ~(x & 0xff00ff00u);
+    uint32_t b0 = ~0u, b1 = ~0u;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll 32
+        for (int j = 0; j < TEST_RATE_ENTRIES / 2; ++j) {
+            const uint2 pp = s_p[j];
+            const uint4 mm = s_m[j];
+            test_min(b0, mm.x, mm.y, nlo, nhi, pp.x);
+            test_min(b1, mm.z, mm.w, nlo, nhi, pp.y);
+        }
+    }
+    if (min(b0, b1) == 0x12345678u) sink[0] = 1u;     // keeps the results live
+}
+
 int launch_reduce_orders(const bn_table* t, const uint32_t* list_best, int B, uint32_t* best_rank, double* score,
                          cudaStream_t s)
 {
@@ -557,6 +606,10 @@ static int score_orders_impl(const bn_table* t, const uint8_t* orders, int B, ui
     if (!orders) return set_error(BN_EINVAL, "bn_score_orders: orders is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const int n = t->n;
+    if (!scan_nodes_fits(t, B)) {
+        int rt = ensure_tuned(t, B, s);
+        if (rt) return rt;
+    }
     const ScanPlan pl = plan_scan(t, B);
     keep_pool_mapped();
 
@@ -640,6 +693,46 @@ extern "C" int bn_score_orders_profiled(const bn_table* t, const uint8_t* orders
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+extern "C" int bn_measure_test_rate(void* stream, double* tests_per_s)
+{
+    set_error(BN_OK, "");
+    if (!tests_per_s) return set_error(BN_EINVAL, "bn_measure_test_rate: NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* sink = nullptr;
+    BN_CUDA(cudaMallocAsync((void**)&sink, 4, s));
+    struct Free {
+        uint32_t* p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{sink, s};
+    cudaEvent_t e0, e1;
+    BN_CUDA(cudaEventCreate(&e0));
+    BN_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev()
+        {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{e0, e1};
+    const unsigned grid = (unsigned)sm_count() * 8u;
+    const uint32_t iters = 16;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {                 // the first launch warms up
+        BN_CUDA(cudaEventRecord(e0, s));
+        k_test_rate<<<grid, 256, 0, s>>>(iters, (uint32_t)rep, sink);
+        BN_LAUNCH_CHECK("k_test_rate");
+        BN_CUDA(cudaEventRecord(e1, s));
+        BN_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    *tests_per_s = (double)grid * 256.0 * iters * TEST_RATE_ENTRIES / (best * 1e-3);
+    return BN_OK;
 }
 
 extern "C" int bn_table_autotune(bn_table* t, int max_items, void* stream, int64_t* chosen)

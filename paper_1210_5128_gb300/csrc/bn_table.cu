@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <set>
+#include <string>
 #include <vector>
 
 #include "bn_table.cuh"
@@ -460,14 +461,23 @@ static int read_status(const uint32_t* d_status, uint32_t* h, cudaStream_t s)
 
 using namespace bn;
 
-extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
-                               const double* R, const bn_score_params* params, int mem,
-                               void* stream, bn_table** out)
+// Host half of a table build: argument checks and the plan of the lgamma tables.
+struct BuildPlan {
+    const uint8_t* data = nullptr;
+    int m = 0, n = 0, k = 0, mem = BN_MEM_HOST, kind = 0;
+    double log10g = 0.0;
+    const double* R = nullptr;
+    std::vector<uint8_t> ar;
+    std::vector<double> Rh;
+    int64_t S = 0;
+    int cells_max = 1;
+    std::vector<int16_t> cell_lut, cfg_lut;
+    std::vector<double> alpha;
+};
+
+static int build_plan(const uint8_t* data, int m, int n, const uint8_t* arity, int k, const double* R,
+                      const bn_score_params* params, int mem, cudaStream_t s, BuildPlan* P)
 {
-    set_error(BN_OK, "");
-    if (!out) return set_error(BN_EINVAL, "bn_build_scores: out is NULL");
-    *out = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
     if (n < 2 || n > MAXN) return set_error(BN_EINVAL, "bn_build_scores: n=%d outside [2, 64]", n);
     if (m < 0 || (m > 0 && !data)) return set_error(BN_EINVAL, "bn_build_scores: bad data/m");
     if (k < 0 || k > n - 1) return set_error(BN_EINVAL, "bn_build_scores: k=%d outside [0, n-1]", k);
@@ -480,9 +490,18 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     if (kind != 0 && kind != 1) return set_error(BN_EINVAL, "bn_build_scores: score_kind %d", kind);
     if (kind == 1 && !(ess > 0.0 && std::isfinite(ess))) return set_error(BN_EINVAL, "bn_build_scores: ess must be > 0");
     if (!std::isfinite(log10g)) return set_error(BN_EINVAL, "bn_build_scores: log10_gamma not finite");
+    P->data = data;
+    P->m = m;
+    P->n = n;
+    P->k = k;
+    P->mem = mem;
+    P->kind = kind;
+    P->log10g = log10g;
+    P->R = R;
     // small arrays are checked on the host
-    std::vector<uint8_t> ar(n);
-    std::vector<double> Rh;
+    std::vector<uint8_t>& ar = P->ar;
+    std::vector<double>& Rh = P->Rh;
+    ar.resize(n);
     if (mem == BN_MEM_DEVICE) {
         BN_CUDA(cudaMemcpyAsync(ar.data(), arity, n, cudaMemcpyDeviceToHost, s));
         if (R) {
@@ -509,6 +528,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     }
     const int64_t S = num_sets_host(n - 1, k);
     if (S >= (int64_t)1 << 31) return set_error(BN_EUNSUPPORTED, "bn_build_scores: %lld sets per node", (long long)S);
+    P->S = S;
     // count-table size bound: r_i times the product of the k largest other arities
     int cells_max = 1;
     for (int i = 0; i < n; ++i) {
@@ -522,6 +542,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
                                             (long long)c, MAX_CELLS);
         cells_max = std::max<int>(cells_max, (int)c);
     }
+    P->cells_max = cells_max;
 
     // LUT plan: K2 uses alpha = 1 for cells and alpha = r for configurations; BDeu uses
     // ess/(q r) and ess/q for every reachable q (products of <= k arities)
@@ -534,8 +555,11 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
         qs.swap(nq);
     }
     const int qmax = *qs.rbegin();
-    std::vector<int16_t> cell_lut((size_t)(qmax + 1) * 5, 0), cfg_lut((size_t)(qmax + 1) * 5, 0);
-    std::vector<double> alpha;
+    std::vector<int16_t>& cell_lut = P->cell_lut;
+    std::vector<int16_t>& cfg_lut = P->cfg_lut;
+    std::vector<double>& alpha = P->alpha;
+    cell_lut.assign((size_t)(qmax + 1) * 5, 0);
+    cfg_lut.assign((size_t)(qmax + 1) * 5, 0);
     if (kind == 0) {
         alpha = {1.0, 2.0, 3.0, 4.0};
         for (int q : qs)
@@ -555,47 +579,44 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
         }
     }
     if (alpha.size() > 32000) return set_error(BN_EUNSUPPORTED, "bn_build_scores: too many lgamma tables");
+    return BN_OK;
+}
 
-    bn_table* t = nullptr;
-    int rc = table_alloc(n, k, &t);
-    if (rc) return rc;
-    struct Guard {
-        bn_table*& t;
-        bool ok = false;
-        ~Guard()
-        {
-            if (!ok && t) bn_table_free(t);
-        }
-    } guard{t};
-
+// Device half: every kernel of the build on stream s, writing t (allocated) and OR-ing
+// STATUS_BADINPUT into *d_status for a data value at or above its arity.  Temporaries
+// are stream-ordered; nothing here waits for the device.
+static int build_enqueue(const BuildPlan& P, bn_table* t, uint32_t* d_status, cudaStream_t s)
+{
+    const int n = P.n, m = P.m, k = P.k;
+    const std::vector<double>& alpha = P.alpha;
+    int rc = BN_OK;
     Temps tmp(s);
     const int mw = (m + 15) / 16;
     uint8_t *d_data = nullptr, *d_ar = nullptr;
-    uint32_t *d_packed = nullptr, *d_status = nullptr;
+    uint32_t* d_packed = nullptr;
     double *d_ppf = nullptr, *d_R = nullptr, *d_alpha = nullptr;
     fx128* d_lut = nullptr;
     int16_t *d_cell = nullptr, *d_cfg = nullptr;
-    if ((rc = tmp.get(&d_ar, n)) || (rc = tmp.get(&d_packed, (size_t)n * mw)) || (rc = tmp.get(&d_status, 1)) ||
+    if ((rc = tmp.get(&d_ar, n)) || (rc = tmp.get(&d_packed, (size_t)n * mw)) ||
         (rc = tmp.get(&d_alpha, alpha.size())) || (rc = tmp.get(&d_lut, alpha.size() * (size_t)(m + 1))) ||
-        (rc = tmp.get(&d_cell, cell_lut.size())) || (rc = tmp.get(&d_cfg, cfg_lut.size())))
+        (rc = tmp.get(&d_cell, P.cell_lut.size())) || (rc = tmp.get(&d_cfg, P.cfg_lut.size())))
         return rc;
-    BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
-    BN_CUDA(cudaMemcpyAsync(d_ar, ar.data(), n, cudaMemcpyHostToDevice, s));
+    BN_CUDA(cudaMemcpyAsync(d_ar, P.ar.data(), n, cudaMemcpyHostToDevice, s));
     BN_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), sizeof(double) * alpha.size(), cudaMemcpyHostToDevice, s));
-    BN_CUDA(cudaMemcpyAsync(d_cell, cell_lut.data(), sizeof(int16_t) * cell_lut.size(), cudaMemcpyHostToDevice, s));
-    BN_CUDA(cudaMemcpyAsync(d_cfg, cfg_lut.data(), sizeof(int16_t) * cfg_lut.size(), cudaMemcpyHostToDevice, s));
+    BN_CUDA(cudaMemcpyAsync(d_cell, P.cell_lut.data(), sizeof(int16_t) * P.cell_lut.size(), cudaMemcpyHostToDevice, s));
+    BN_CUDA(cudaMemcpyAsync(d_cfg, P.cfg_lut.data(), sizeof(int16_t) * P.cfg_lut.size(), cudaMemcpyHostToDevice, s));
     if (m > 0) {
-        if (mem == BN_MEM_DEVICE) d_data = (uint8_t*)data;
+        if (P.mem == BN_MEM_DEVICE) d_data = (uint8_t*)P.data;
         else {
             if ((rc = tmp.get(&d_data, (size_t)m * n))) return rc;
-            if ((rc = copy_in(d_data, data, (size_t)m * n, BN_MEM_HOST, s))) return rc;
+            if ((rc = copy_in(d_data, P.data, (size_t)m * n, BN_MEM_HOST, s))) return rc;
         }
         k_pack<<<(n * mw + 255) / 256, 256, 0, s>>>(d_data, m, n, mw, d_ar, d_packed, d_status);
         BN_LAUNCH_CHECK("k_pack");
     }
-    if (R) {
+    if (P.R) {
         if ((rc = tmp.get(&d_ppf, (size_t)n * n)) || (rc = tmp.get(&d_R, (size_t)n * n))) return rc;
-        BN_CUDA(cudaMemcpyAsync(d_R, Rh.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
+        BN_CUDA(cudaMemcpyAsync(d_R, P.Rh.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
         k_ppf<<<(n * n + 255) / 256, 256, 0, s>>>(d_R, n, d_ppf);
         BN_LAUNCH_CHECK("k_ppf");
     }
@@ -612,14 +633,14 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     A.n = n;
     A.mw = mw;
     A.k = k;
-    A.S = S;
+    A.S = P.S;
     A.Sp = t->Sp;
-    A.units_per_node = (int)((S + BUILD_RANGE - 1) / BUILD_RANGE);
-    A.cells_cap = (int)round_up(cells_max, 32);
-    A.cells_max = (int)cells_max;
+    A.units_per_node = (int)((P.S + BUILD_RANGE - 1) / BUILD_RANGE);
+    A.cells_cap = (int)round_up(P.cells_max, 32);
+    A.cells_max = (int)P.cells_max;
     A.arity = d_ar;
     A.ppf = d_ppf;
-    A.log10g = log10g;
+    A.log10g = P.log10g;
     A.lut = d_lut;
     A.lut_stride = m + 1;
     A.cell_lut = d_cell;
@@ -642,12 +663,133 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
         default: rc = launch_build_kt<12>(A, smem_data, smem, grid, s); break;
     }
     if (rc) return rc;
-    if ((rc = rank_entries(t, s))) return rc;
-    uint32_t st = 0;
-    if ((rc = read_status(d_status, &st, s))) return rc;
-    if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_build_scores: a data value is >= its arity");
+    return rank_entries(t, s);
+}
+
+extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                               const double* R, const bn_score_params* params, int mem,
+                               void* stream, bn_table** out)
+{
+    set_error(BN_OK, "");
+    if (!out) return set_error(BN_EINVAL, "bn_build_scores: out is NULL");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    BuildPlan P;
+    int rc = build_plan(data, m, n, arity, k, R, params, mem, s, &P);
+    if (rc) return rc;
+    bn_table* t = nullptr;
+    if ((rc = table_alloc(n, k, &t))) return rc;
+    struct Guard {
+        bn_table*& t;
+        bool ok = false;
+        ~Guard()
+        {
+            if (!ok && t) bn_table_free(t);
+        }
+    } guard{t};
+    uint32_t* d_status = nullptr;
+    {
+        Temps tmp(s);
+        if ((rc = tmp.get(&d_status, 1))) return rc;
+        BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+        if ((rc = build_enqueue(P, t, d_status, s))) return rc;
+        uint32_t st = 0;
+        if ((rc = read_status(d_status, &st, s))) return rc;
+        if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_build_scores: a data value is >= its arity");
+    }
     guard.ok = true;
     *out = t;
+    return BN_OK;
+}
+
+extern "C" int bn_build_scores_batch(int count, const uint8_t* const* data, const int* m, const int* n,
+                                     const uint8_t* const* arity, const int* k, const double* const* R,
+                                     const bn_score_params* params, int mem, void* stream, bn_table** out)
+{
+    set_error(BN_OK, "");
+    if (count < 1 || !data || !m || !n || !arity || !k || !out)
+        return set_error(BN_EINVAL, "bn_build_scores_batch: bad arguments");
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<BuildPlan> plans(count);
+    for (int i = 0; i < count; ++i) {
+        int rc = build_plan(data[i], m[i], n[i], arity[i], k[i], R ? R[i] : nullptr, params ? &params[i] : nullptr,
+                            mem, s, &plans[i]);
+        if (rc) {
+            std::string msg = bn_last_error();
+            return set_error(rc, "bn_build_scores_batch: network %d: %s", i, msg.c_str());
+        }
+    }
+    std::vector<bn_table*> tabs(count, nullptr);
+    struct Guard {
+        std::vector<bn_table*>& t;
+        bool ok = false;
+        ~Guard()
+        {
+            if (!ok)
+                for (bn_table* x : t) bn_table_free(x);
+        }
+    } guard{tabs};
+    for (int i = 0; i < count; ++i) {
+        int rc = table_alloc(n[i], k[i], &tabs[i]);
+        if (rc) return rc;
+    }
+    // the builds run on a few side streams that fork from and join into `stream`; the
+    // largest networks are spread over the streams first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)n[a] * (double)plans[a].S * (double)(m[a] + 1) > (double)n[b] * (double)plans[b].S * (double)(m[b] + 1);
+    });
+    const int ns = std::min(count, 4);
+    std::vector<cudaStream_t> side(ns, nullptr);
+    std::vector<cudaEvent_t> ev(ns + 1, nullptr);
+    struct Streams {
+        std::vector<cudaStream_t>& s;
+        std::vector<cudaEvent_t>& e;
+        ~Streams()
+        {
+            for (cudaStream_t x : s)
+                if (x) cudaStreamDestroy(x);
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } sg{side, ev};
+    uint32_t* d_status = nullptr;
+    BN_CUDA(cudaMallocAsync((void**)&d_status, sizeof(uint32_t) * count, s));
+    struct Free {
+        uint32_t* p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{d_status, s};
+    BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t) * count, s));
+    for (int j = 0; j <= ns; ++j) BN_CUDA(cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming));
+    BN_CUDA(cudaEventRecord(ev[ns], s));
+    for (int j = 0; j < ns; ++j) {
+        BN_CUDA(cudaStreamCreateWithFlags(&side[j], cudaStreamNonBlocking));
+        BN_CUDA(cudaStreamWaitEvent(side[j], ev[ns], 0));
+    }
+    int rc = BN_OK;
+    for (int q = 0; q < count && !rc; ++q) {
+        const int i = order[q];
+        rc = build_enqueue(plans[i], tabs[i], d_status + i, side[q % ns]);
+    }
+    for (int j = 0; j < ns; ++j) {
+        cudaEventRecord(ev[j], side[j]);
+        cudaStreamWaitEvent(s, ev[j], 0);
+    }
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    std::vector<uint32_t> st(count, 0);
+    BN_CUDA(cudaMemcpyAsync(st.data(), d_status, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i)
+        if (st[i] & STATUS_BADINPUT)
+            return set_error(BN_EINVAL, "bn_build_scores_batch: network %d: a data value is >= its arity", i);
+    guard.ok = true;
+    for (int i = 0; i < count; ++i) out[i] = tabs[i];
     return BN_OK;
 }
 

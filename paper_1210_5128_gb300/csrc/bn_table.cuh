@@ -57,6 +57,8 @@ struct ScanPlan {
     int sub = 1024;    // entries per shared-memory stage (512, 1024 or 2048)
 };
 ScanPlan plan_scan(const bn_table* t, int max_items);
+// tune the full-table scan's tiling for up to max_items items on first use (bn_scan.cu)
+int ensure_tuned(const bn_table* t, int max_items, cudaStream_t s);
 
 constexpr uint32_t SPOS_NONE = 0xffffffffu;
 

@@ -131,12 +131,10 @@ WORKLOADS = {
     "n20_k4_m1000": dict(n=20, arity=3, max_indeg=3, m=1000, k=4, prior=(0.1, 0.1), seed_index=1),
     # 40 ternary nodes, 2000 samples, k = 4
     "n40_k4_m2000": dict(n=40, arity=3, max_indeg=3, m=2000, k=4, prior=None, seed_index=2),
+    # 40 ternary nodes, 1000 samples, k = 4 (fewer surviving parent sets than with 2000)
+    "n40_k4_m1000": dict(n=40, arity=3, max_indeg=3, m=1000, k=4, prior=None, seed_index=5),
     # 60 ternary nodes, 1000 samples, k = 4 (the paper's largest graph)
     "n60_k4_m1000": dict(n=60, arity=3, max_indeg=3, m=1000, k=4, prior=None, seed_index=3),
-    # the n = 40 and n = 60 table shapes (k = 4) on binary data with 200 samples: tables the
-    # CPU oracle builds in seconds on a few host threads, for the full-size parity tests
-    "n40_k4_m200_bin": dict(n=40, arity=2, max_indeg=3, m=200, k=4, prior=None, seed_index=6),
-    "n60_k4_m200_bin": dict(n=60, arity=2, max_indeg=3, m=200, k=4, prior=None, seed_index=7),
 }
 
 

@@ -110,18 +110,48 @@ def test_batch_network_vs_oracle(gpu):
     assert np.array_equal(gpu.chains_read(b.chains(1), "trace_score"), ref6["trace_score"])
 
 
-def test_batch_with_a_learned_network(gpu):
-    nets = _nets(3, 5)
+def test_batch_with_learned_networks_equals_networks_alone(gpu):
+    """Networks switched to the learned proposal (one trained on its own chains' history
+    first) step through their own path inside the batch while the others share the fused
+    launch; every network's results equal stepping it alone with the same proposal."""
+    nets = _nets(4, 5)
     tables = []
     for data, ar, k in nets:
         t = gpu.build_scores(data, ar, k)
         gpu.table_set_scan(t, gpu.SCAN_PRUNED)
         tables.append(t)
-    b = gpu.batch_create(tables, 16, 9)
-    n1 = gpu.table_info(tables[1])["n"]
-    net = gpu.mlp_create(n1, synth.mlp_init_weights(n1, 8, 128, 2), hidden=128, d=8, batch_cap=16)
-    gpu.chains_set_proposal(b.chains(1), net, gpu.PROPOSAL_LEARNED, eps_mix=0.2)
+    chains = [16, 24, 8, 32]
+    seeds = [9, 10, 11, 12]
+    learned = {1: 0.2, 3: 0.1}                         # network -> eps_mix
+
+    def weights(i):
+        n = gpu.table_info(tables[i])["n"]
+        return n, synth.mlp_init_weights(n, 8, 128, 2 + i)
+
+    b = gpu.batch_create(tables, chains, seeds, burn_in=30, trace_cap=300)
+    keep = []
+    for i, eps in learned.items():
+        n, w = weights(i)
+        net = gpu.mlp_create(n, w, hidden=128, d=8, batch_cap=chains[i], lr=1e-3)
+        keep.append(net)
+        if i == 3:                                    # trained on its own history first
+            gpu.chains_set_proposal(b.chains(i), net, gpu.PROPOSAL_TRAIN, eps_mix=eps)
+            gpu.chains_step(b.chains(i), 100)
+        gpu.chains_set_proposal(b.chains(i), net, gpu.PROPOSAL_LEARNED, eps_mix=eps)
     b.step(200)
-    for i in range(3):
-        assert gpu.chains_read(b.chains(i), "steps")[0] == 200
+    for i, t in enumerate(tables):
+        alone = gpu.chains_create(t, chains[i], seeds[i], burn_in=30, trace_cap=300)
+        if i in learned:
+            n, w = weights(i)
+            net = gpu.mlp_create(n, w, hidden=128, d=8, batch_cap=chains[i], lr=1e-3)
+            keep.append(net)
+            if i == 3:
+                gpu.chains_set_proposal(alone, net, gpu.PROPOSAL_TRAIN, eps_mix=learned[i])
+                gpu.chains_step(alone, 100)
+            gpu.chains_set_proposal(alone, net, gpu.PROPOSAL_LEARNED, eps_mix=learned[i])
+            gpu.chains_step(alone, 200)
+        else:
+            gpu.chains_step(alone, 200)
+        for what in OUTS:
+            assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
         assert gpu.chains_read(b.chains(i), "accepts").max() > 0

@@ -6,15 +6,17 @@ n = 60 (k = 4), where a swap's span can exceed the 32 lanes of a warp (lane l th
 span positions a + l and a + l + 32):
 
 - n = 40: traced and untraced runs against the oracle's own sampler on the oracle's own
-  table, step for step (scores, accept flags, final and best states, edge counts);
+  table, step for step (scores, accept flags, final and best states, edge counts), with
+  the survivors in shared memory (m = 1000) and in the cache's global-memory copy
+  (m = 2000, more survivors than shared memory holds);
 - n = 60: the bench's shape, 256 chains in two untraced 1,000-step launches, against the
   full-table sampler (three kernels per step, no pruning) bit for bit, the final and
   best orders of a sample of chains re-scored by the oracle, and the first steps of 16
   chains against the oracle's trajectories.
 
-The tables are built by the oracle (binary data, 200 samples: the n = 40 and n = 60 table
-shapes in seconds on the host's cores); the n = 60 one is also compared with the GPU's
-build of the same data, every entry."""
+The tables are the workloads' own (n = 40: 3 states, m = 1000 and 2000; n = 60: 3 states,
+m = 1000, the bench's table), every entry built by the oracle on the host's cores; the
+n = 60 one is also compared with the GPU's build of the same data, every entry."""
 import numpy as np
 import pytest
 
@@ -26,21 +28,6 @@ pytestmark = pytest.mark.gpu
 SURV_CACHE_MAX = 2400          # survivors a network may have for the shared-memory cache
 OUTS = ("orders", "scores", "ranks", "best_scores", "best_orders", "best_ranks", "accepts", "edge_counts",
         "steps", "items")
-
-
-def _oracle_table(name):
-    data, arity, k, R, _ = synth.workload(name)
-    return data, arity, k, R, oracle.build_table(data, arity, k, R=R, threads=None)
-
-
-@pytest.fixture(scope="module")
-def n40():
-    return _oracle_table("n40_k4_m200_bin")
-
-
-@pytest.fixture(scope="module")
-def n60():
-    return _oracle_table("n60_k4_m200_bin")
 
 
 def _spans(n, seed, chains, steps):
@@ -56,21 +43,26 @@ def _spans(n, seed, chains, steps):
     return out
 
 
-def _pruned_staged(gpu, tab, k):
+def _pruned(gpu, tab, k, staged=True):
+    """The oracle's table, pruned; staged: its survivors fit the fused kernel's
+    shared-memory cache (else they run from the global-memory copy of the cache)."""
     t = gpu.table_from_scores(tab, k)
     gpu.table_set_scan(t, gpu.SCAN_PRUNED)
-    surv = gpu.table_pruned(t)
-    # the shared-memory cache variant of the fused kernel runs for this table
-    assert 0 < int(surv.sum()) <= SURV_CACHE_MAX, int(surv.sum())
+    surv = int(gpu.table_pruned(t).sum())
+    assert surv > 0 and (surv <= SURV_CACHE_MAX) == staged, surv
     return t
 
 
-def test_n40_fused_sampler_against_oracle(gpu, n40):
-    data, arity, k, R, tab = n40
+@pytest.mark.parametrize("which,staged", [("oracle_n40_m1000", True), ("oracle_n40", False)])
+def test_n40_fused_sampler_against_oracle(gpu, request, which, staged):
+    """n = 40 with 1,000 samples (survivors in shared memory) and with 2,000 samples (more
+    survivors than the shared-memory cache holds: the same walk over the cache's
+    global-memory copy)."""
+    data, arity, k, R, tab = request.getfixturevalue(which)
     n = tab.shape[0]
     chains, steps, seed, burn = 8, 60, 4040, 10
     assert (_spans(n, seed, chains, steps) > 32).sum() >= 5      # the lane-half path runs
-    t = _pruned_staged(gpu, tab, k)
+    t = _pruned(gpu, tab, k, staged)
     ref = oracle.mcmc_run(tab, k, chains, steps, seed=seed, burn_in=burn, trace=True, threads=None)
     traced = gpu.chains_create(t, chains, seed, burn_in=burn, trace_cap=steps)
     gpu.chains_step(traced, steps)
@@ -89,20 +81,20 @@ def test_n40_fused_sampler_against_oracle(gpu, n40):
     assert ref["accepts"].sum() > 0
 
 
-def test_n60_table_every_entry(gpu, n60):
-    data, arity, k, R, tab = n60
+def test_n60_table_every_entry(gpu, oracle_n60):
+    data, arity, k, R, tab = oracle_n60
     t = gpu.build_scores(data, arity, k, R=R)
     np.testing.assert_allclose(gpu.table_scores(t), tab, rtol=1e-12, atol=1e-12)
 
 
-def test_n60_first_steps_against_oracle(gpu, n60):
+def test_n60_first_steps_against_oracle(gpu, oracle_n60):
     """16 chains, 5 steps each, traced, against the oracle's trajectories (an oracle step
     at n = 60 is a full brute-force order score, about a second of CPU time)."""
-    _, _, k, _, tab = n60
+    _, _, k, _, tab = oracle_n60
     n = tab.shape[0]
     chains, steps, seed = 16, 5, 6060
     assert (_spans(n, seed, chains, steps) > 32).sum() >= 5
-    t = _pruned_staged(gpu, tab, k)
+    t = _pruned(gpu, tab, k)
     ch = gpu.chains_create(t, chains, seed, trace_cap=steps)
     gpu.chains_step(ch, steps)
     ref = oracle.mcmc_run(tab, k, chains, steps, seed=seed, trace=True, threads=None)
@@ -112,10 +104,10 @@ def test_n60_first_steps_against_oracle(gpu, n60):
     assert np.array_equal(gpu.chains_read(ch, "best_ranks"), ref["best_rank"])
 
 
-def test_n60_headline_launches_equal_full_table_and_oracle(gpu, n60):
+def test_n60_headline_launches_equal_full_table_and_oracle(gpu, oracle_n60):
     """The bench's shape: 256 chains, untraced, two 1,000-step calls (one fused launch
     each) against the unpruned full-table sampler over the same 2,000 steps."""
-    _, _, k, _, tab = n60
+    _, _, k, _, tab = oracle_n60
     n = tab.shape[0]
     chains, seed, burn = 256, 60256, 100
     spans = _spans(n, seed, 2, 200)
@@ -123,7 +115,7 @@ def test_n60_headline_launches_equal_full_table_and_oracle(gpu, n60):
     full_t = gpu.table_from_scores(tab, k)
     full = gpu.chains_create(full_t, chains, seed, burn_in=burn)
     gpu.chains_step(full, 2000)
-    t = _pruned_staged(gpu, tab, k)
+    t = _pruned(gpu, tab, k)
     fused = gpu.chains_create(t, chains, seed, burn_in=burn)
     for _ in range(2):
         gpu.chains_step(fused, 1000)

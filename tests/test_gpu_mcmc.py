@@ -119,3 +119,68 @@ def test_ess_matches_oracle_on_recorded_series(gpu):
                 assert ess[i, m] == pytest.approx(tot, rel=1e-9)
             else:
                 assert np.isnan(ess[i, m])
+
+
+def test_mcmc_run_stats_uniform(gpu):
+    """bn_mcmc_run's summary equals what the chain API reads for the same run: acceptance
+    over the steps and the ESS median/min over the uncertain edges."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    tab = oracle.build_table(data, arity, k, R=R)
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    C, steps, burn = 16, 3000, 300
+    out = gpu.mcmc_run(t, C, steps, seed=8, burn_in=burn, thin=2)
+    st = out["stats"]
+    ch = gpu.chains_create(t, C, 8, burn_in=burn, record_every=2, record_cap=(steps - burn + 1) // 2)
+    gpu.chains_step(ch, steps)
+    acc = gpu.chains_read(ch, "accepts")
+    assert st["acceptance"] == acc.sum() / (C * steps)
+    f = gpu.chains_read(ch, "edge_counts").sum(0) / (C * (steps - burn))
+    np.testing.assert_array_equal(out["edge_freq"], f)
+    ess = gpu.chains_read(ch, "ess")
+    unc = (f >= 0.05) & (f <= 0.95) & ~np.isnan(ess)
+    assert st["uncertain_edges"] == unc.sum() > 0
+    assert st["ess_median"] == np.median(ess[unc]) and st["ess_min"] == ess[unc].min()
+    assert st["order_evals"] == C * steps and st["sample_ms"] > 0 and st["train_ms"] == 0
+    s_ref, r_ref = oracle.order_score(tab, k, out["best_order"])
+    assert out["best_score"] == s_ref
+    assert np.array_equal(out["best_dag"], oracle.greedy_dag(20, k, r_ref))
+
+
+def test_mcmc_run_learned_proposal(gpu):
+    """The learned sampler through the one-shot call: train_iters training steps, then
+    the learned proposal; the same run through the chain API gives the same results."""
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    tab = oracle.build_table(data, arity, k, R=R)
+    t = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    C, train, steps, burn = 32, 200, 600, 100
+    w = synth.mlp_init_weights(20, 8, 128, 4)
+    net_a = gpu.mlp_create(20, w, hidden=128, d=8, batch_cap=C, lr=1e-3)
+    out = gpu.mcmc_run(t, C, steps, seed=9, burn_in=burn, proposal=gpu.PROPOSAL_LEARNED, eps_mix=0.2,
+                       train_iters=train, thin=1, net=net_a)
+    st = out["stats"]
+    assert 0 < st["acceptance"] < 1 and st["order_evals"] == C * (train + steps)
+    assert st["train_ms"] > 0 and st["sample_ms"] > 0
+    net_b = gpu.mlp_create(20, w, hidden=128, d=8, batch_cap=C, lr=1e-3)
+    ch = gpu.chains_create(t, C, 9, burn_in=burn)
+    gpu.chains_set_proposal(ch, net_b, gpu.PROPOSAL_TRAIN, eps_mix=0.2)
+    gpu.chains_step(ch, train)
+    gpu.chains_set_proposal(ch, net_b, gpu.PROPOSAL_LEARNED, eps_mix=0.2)
+    a0 = gpu.chains_read(ch, "accepts").copy()
+    gpu.chains_step(ch, steps)
+    f = gpu.chains_read(ch, "edge_counts").sum(0) / (C * (train + steps - burn))
+    np.testing.assert_array_equal(out["edge_freq"], f)
+    assert st["acceptance"] == (gpu.chains_read(ch, "accepts") - a0).sum() / (C * steps)
+    c = int(np.argmax(gpu.chains_read(ch, "best_scores")))
+    assert out["best_score"] == gpu.chains_read(ch, "best_scores")[c]
+    s_ref, r_ref = oracle.order_score(tab, k, out["best_order"])
+    assert out["best_score"] == s_ref
+    assert np.array_equal(out["best_dag"], oracle.greedy_dag(20, k, r_ref))
+    # the network the call creates itself (d = 32, H = 512)
+    out2 = gpu.mcmc_run(t, C, 200, seed=10, proposal=gpu.PROPOSAL_LEARNED, eps_mix=0.1, train_iters=100, thin=1)
+    assert out2["stats"]["order_evals"] == C * 300 and 0 < out2["stats"]["acceptance"] < 1
+    with pytest.raises(gpu.BNError):
+        gpu.mcmc_run(t, C, 10, seed=1, proposal=7)
+    with pytest.raises(gpu.BNError):
+        gpu.mcmc_run(t, C, 10, seed=1, proposal=gpu.PROPOSAL_LEARNED, eps_mix=0.0)

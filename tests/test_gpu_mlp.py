@@ -75,10 +75,38 @@ def test_gradients_and_adam_match_oracle(gpu, n, d, H, B):
     pairs = rng.integers(0, n * (n - 1) // 2, B).astype(np.uint32)
     alpha = rng.uniform(0, 1, B).astype(np.float32)
     loss = gpu.mlp_loss_grad(net, orders, pairs, alpha)
-    ref_loss, ref_g = omlp.mlp_loss_grad(prm, orders, pairs.astype(np.int64), alpha.astype(np.float64))
+    ref_loss, ref_g = omlp.mlp_loss_grad(prm, orders, pairs.astype(np.int64), alpha.astype(np.float64),
+                                         with_terms=True)
     assert loss == pytest.approx(ref_loss, rel=1e-4)
+    # Every gradient is a sum over the batch of per-example terms of either sign, so its
+    # rounding error scales with the sum of the terms' magnitudes (the usual bound for a
+    # floating-point sum), not with the sum itself when terms cancel: the norm bar is
+    # taken relative to that magnitude sum, from the oracle's per-example factors.
+    T = {key: np.abs(v) for key, v in ref_g["terms"].items()}
+    pr = pairs.astype(np.int64)
+    mag = {"W1": T["dz1"].T @ T["x"], "b1": T["dz1"].sum(0), "W2": T["dz2"].T @ T["h1"], "b2": T["dz2"].sum(0),
+           "W3": np.zeros_like(ref_g["W3"]), "b3": np.zeros_like(ref_g["b3"]), "E": np.zeros_like(ref_g["E"])}
+    np.add.at(mag["W3"], pr, T["dl"][:, None] * T["h2"])
+    np.add.at(mag["b3"], pr, T["dl"])
+    np.add.at(mag["E"], np.asarray(orders, np.int64).reshape(-1), T["dx"].reshape(-1, d))
+    # ReLU decisions the kernels take in FP32 and the oracle in FP64: a pre-activation
+    # within FP32 accumulation error of zero (2^-16 of its terms' magnitude sum, ten times
+    # the sqrt(K) 2^-24 typical of K <= 2048 terms) may fall on either side, and then the
+    # term it gates in the weight and bias gradients is present on one side only.  Either
+    # is valid: the element bar grows by those terms' magnitudes (first order).
+    tau = 2.0 ** -16
+    near1 = np.abs(ref_g["terms"]["z1"]) <= tau * (T["x"] @ T["W1"].T + np.abs(w["b1"]))
+    near2 = np.abs(ref_g["terms"]["z2"]) <= tau * (T["h1"] @ T["W2"].T + np.abs(w["b2"]))
+    assert near1.mean() < 1e-2 and near2.mean() < 1e-2, (near1.sum(), near2.sum())
+    g1 = near1 * T["dh1"]
+    g2 = near2 * T["dh2"]
+    extra = {"W1": g1.T @ T["x"], "b1": g1.sum(0), "W2": g2.T @ T["h1"], "b2": g2.sum(0)}
     for name in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]:
-        _close(gpu.mlp_read(net, name, grad=True), ref_g[name], elem=GRAD_ELEM, norm=GRAD_NORM)
+        g = gpu.mlp_read(net, name, grad=True).astype(np.float64)
+        ref = ref_g[name]
+        bound = GRAD_ELEM * np.abs(ref).max() + extra.get(name, 0.0)
+        assert (np.abs(g - ref) <= bound).all(), (name, (np.abs(g - ref) - bound).max())
+        assert np.linalg.norm(g - ref) <= GRAD_NORM * np.linalg.norm(mag[name]), name
     lr, eps = 1e-3, 1e-8
     gpu.mlp_adam_step(net)
     for name in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]:
@@ -86,12 +114,13 @@ def test_gradients_and_adam_match_oracle(gpu, n, d, H, B):
         upd = gpu.mlp_read(net, name).astype(np.float64) - before.astype(np.float64)
         # Adam's first step (m, v from zero, bias-corrected) is -lr g / (|g| + eps), a
         # monotone function of g.  The gradient check above bounds every element of the
-        # kernel's gradient within delta of the oracle's, so each update must lie between
+        # kernel's gradient within delta (its element bar) of the oracle's, so each update
+        # must lie between
         # the steps of g_ref - delta and g_ref + delta -- a tight bound wherever
         # |g_ref| >> delta, and one that admits either sign only where it is within delta
         # of zero.  Slack: FP32 rounding of the step and of the updated weight.
         g = ref_g[name]
-        delta = GRAD_ELEM * np.abs(g).max()
+        delta = GRAD_ELEM * np.abs(g).max() + extra.get(name, 0.0)
         step = lambda x: -lr * x / (np.abs(x) + eps)            # noqa: E731
         lo, hi = step(g + delta), step(g - delta)
         slack = 1e-6 * lr + 2.0 * np.spacing(np.abs(before)).astype(np.float64)

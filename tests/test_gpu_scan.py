@@ -182,10 +182,9 @@ def test_unranked_parent_sets_against_oracle(gpu, name, B):
     _check_shared(gpu, tab, k, synth.random_orders(data.shape[1], B, 55 + B), mode=gpu.SCAN_UNRANK)
 
 
-def test_unranked_n40_against_oracle(gpu):
-    """The unranked scan at the n = 40 table shape (k = 4) on the oracle's table."""
-    data, arity, k, R, _ = synth.workload("n40_k4_m200_bin")
-    tab = oracle.build_table(data, arity, k, R=R, threads=None)
+def test_unranked_n40_against_oracle(gpu, oracle_n40):
+    """The unranked scan on the oracle's table of the 40-node workload (k = 4)."""
+    _, _, k, _, tab = oracle_n40
     t = gpu.table_from_scores(tab, k)
     gpu.table_set_scan(t, gpu.SCAN_UNRANK)
     orders = synth.random_orders(40, 64, 4)

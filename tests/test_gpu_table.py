@@ -113,3 +113,26 @@ def test_bad_data_value_on_device_rejected(gpu):
     with pytest.raises(gpu.BNError) as e:
         gpu.build_scores(data, np.array([2, 2, 3], np.uint8), 1)
     assert e.value.code == gpu.EINVAL
+
+
+def test_batch_build_equals_single_builds(gpu):
+    """bn_build_scores_batch (builds on concurrent streams) gives each network the table
+    bn_build_scores gives it, entry for entry, with sorted positions that score orders the
+    same; the smallest network is pinned to the oracle; a bad network is named."""
+    nets = synth.uneven_batch(10, 0xB4E5_0B0B)
+    tabs = gpu.build_scores_batch([(d, a, k, R) for d, a, k, R, _ in nets])
+    for (d, a, k, R, _), t in zip(nets, tabs):
+        single = gpu.build_scores(d, a, k, R=R)
+        assert np.array_equal(gpu.table_scores(t), gpu.table_scores(single))
+        orders = synth.random_orders(d.shape[1], 40, 3)
+        r1, s1 = gpu.score_orders(t, orders)
+        r2, s2 = gpu.score_orders(single, orders)
+        assert np.array_equal(r1, r2) and np.array_equal(s1, s2)
+    i = int(np.argmin([d.shape[1] for d, *_ in nets]))
+    d, a, k, R, _ = nets[i]
+    _cmp(gpu.table_scores(tabs[i]), oracle.build_table(d, a, k, R=R, threads=None))
+    bad = [(nets[0][0], nets[0][1], nets[0][2], None),
+           (np.full((5, 3), 7, np.uint8), np.array([2, 2, 2], np.uint8), 1, None)]
+    with pytest.raises(gpu.BNError) as e:
+        gpu.build_scores_batch(bad)
+    assert e.value.code == gpu.EINVAL and "network 1" in str(e.value)
