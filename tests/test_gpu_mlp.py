@@ -89,12 +89,15 @@ def test_gradients_and_adam_match_oracle(gpu, n, d, H, B):
     np.add.at(mag["W3"], pr, T["dl"][:, None] * T["h2"])
     np.add.at(mag["b3"], pr, T["dl"])
     np.add.at(mag["E"], np.asarray(orders, np.int64).reshape(-1), T["dx"].reshape(-1, d))
-    # ReLU decisions the kernels take in FP32 and the oracle in FP64: a pre-activation
-    # within FP32 accumulation error of zero (2^-16 of its terms' magnitude sum, ten times
-    # the sqrt(K) 2^-24 typical of K <= 2048 terms) may fall on either side, and then the
-    # term it gates in the weight and bias gradients is present on one side only.  Either
-    # is valid: the element bar grows by those terms' magnitudes (first order).
-    tau = 2.0 ** -16
+    # ReLU decisions the kernels take in FP32 and the oracle in FP64: the kernels' sums
+    # differ from the oracle's by FP32 accumulation (K 2^-24 of the terms' magnitude sum,
+    # at most 2^-13 for K <= 2048) and, for layer 2, by layer-1 outputs whose bf16 rounding
+    # fell the other way (each one ulp, 2^-8 of its term; measured up to 4e-5 of the sum).
+    # A pre-activation within 2^-13 of its magnitude sum of zero may therefore fall on
+    # either side, and then the term it gates in the weight and bias gradients is present
+    # on one side only.  Either is valid: the element bar grows by those terms'
+    # magnitudes (first order).
+    tau = 2.0 ** -13
     near1 = np.abs(ref_g["terms"]["z1"]) <= tau * (T["x"] @ T["W1"].T + np.abs(w["b1"]))
     near2 = np.abs(ref_g["terms"]["z2"]) <= tau * (T["h1"] @ T["W2"].T + np.abs(w["b2"]))
     assert near1.mean() < 1e-2 and near2.mean() < 1e-2, (near1.sum(), near2.sum())
