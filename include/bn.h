@@ -421,6 +421,21 @@ void bn_mlp_free(bn_mlp* m);
 #define BN_PROPOSAL_TRAIN   2
 int bn_chains_set_proposal(bn_chains* c, bn_mlp* m, int mode, double eps_mix, void* stream);
 
+/* How the learned proposal's steps on a pruned table are launched (the results are the
+ * same either way):
+ *   BN_LEARNED_LAUNCH_AUTO   (default) one cooperative persistent kernel runs up to 256
+ *                            steps per launch -- per step the layer-2 tiles, the output-layer
+ *                            tiles and the chains, separated by grid-wide barriers, with the
+ *                            weight tiles resident in shared memory and TMEM -- when all its
+ *                            CTAs fit on the GPU at once (at most 256 chains at H = 512);
+ *                            otherwise as BN_LEARNED_LAUNCH_GRAPH
+ *   BN_LEARNED_LAUNCH_GRAPH  three kernels per step (chains, layer 2, output layer),
+ *                            chained by programmatic dependent launch in a CUDA graph
+ * Errors: BN_EINVAL. */
+#define BN_LEARNED_LAUNCH_AUTO  0
+#define BN_LEARNED_LAUNCH_GRAPH 1
+int bn_chains_set_learned_launch(bn_chains* c, int mode);
+
 /* C (M x N float32) = A (M x K bf16) * B (N x K bf16)^T on the tensor cores (tcgen05,
  * TMEM accumulator); device pointers, row-major, M and N multiples of 128, K of 64.
  * The proposal network's dense-layer GEMM, exposed for testing. */

@@ -100,6 +100,7 @@ def _load():
     _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp,
                                C.POINTER(MCMCStats), _vp]
     _L.bn_measure_test_rate.argtypes = [_vp, C.POINTER(C.c_double)]
+    _L.bn_chains_set_learned_launch.argtypes = [_vp, C.c_int]
     _L.bn_mlp_create.argtypes = [C.c_int, C.POINTER(MLPParams)] + [_vp] * 7 + [C.c_int, _vp, C.POINTER(_vp)]
     _L.bn_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp, C.c_int, _vp]
     _L.bn_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_int, _vp]
@@ -594,6 +595,15 @@ def chains_set_proposal(c: Chains, mlp, mode, eps_mix=0.1, stream=None):
     c.mlp = mlp                 # keeps the network alive with the chains
     _check(lib().bn_chains_set_proposal(c.handle, mlp.handle if mlp is not None else None, mode, eps_mix,
                                         stream))
+
+
+LEARNED_LAUNCH_AUTO, LEARNED_LAUNCH_GRAPH = 0, 1
+
+
+def chains_set_learned_launch(c: Chains, mode):
+    """Persistent cooperative launch (AUTO, when it fits) or three kernels per step from a
+    CUDA graph (GRAPH) for the learned proposal; the results are the same."""
+    _check(lib().bn_chains_set_learned_launch(c.handle, mode))
 
 
 def gemm_bf16(A, B):

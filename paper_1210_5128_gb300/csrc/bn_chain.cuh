@@ -210,5 +210,6 @@ struct bn_chains {
     int dev = 0;
     bn::LearnedPath* lp = nullptr;  // fast learned-proposal path (bn_learned.cu)
     bool lq_valid = false;          // S.cur_lq matches the current orders (graph path)
+    int learned_launch = BN_LEARNED_LAUNCH_AUTO;   // bn_chains_set_learned_launch
 };
 

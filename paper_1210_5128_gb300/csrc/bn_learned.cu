@@ -247,6 +247,49 @@ __host__ __device__ constexpr size_t lgemm_smem(int K)
     return (size_t)LR_TM * K * 2 + (size_t)LR_TN * K * 2 + 8 * (size_t)(K / 64 + 1) + 16 + 1024;
 }
 
+// epilogue of one 128 x 32 tile: TMEM -> bias (+ ReLU -> bf16 operand of the next layer, or
+// logits + per-tile softmax partials of the output layer); warp w holds rows 32w..32w+31
+__device__ __forceinline__ void lgemm_epilogue(const LGemmArgs& g, uint32_t tmem, int warp, int lane, int mt, int nt)
+{
+    uint32_t r[32];
+    tc_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16), r);
+    tc_wait_ld();
+    const int row = mt * LR_TM + warp * 32 + lane;
+    const int n0 = nt * LR_TN;
+    if (g.mode == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = fmaxf(__uint_as_float(r[q * 8 + j]) + g.bias[n0 + q * 8 + j], 0.f);
+            uint4 o;
+            o.x = pack_bf16x2(v[0], v[1]);
+            o.y = pack_bf16x2(v[2], v[3]);
+            o.z = pack_bf16x2(v[4], v[5]);
+            o.w = pack_bf16x2(v[6], v[7]);
+            *(uint4*)(g.out_h + cm_off(row, n0 + q * 8, g.K, LR_TM)) = o;
+        }
+    } else if (row < g.C) {
+        const int cb = g.cur_buf[row];
+        const int buf = g.prime ? cb : 1 - cb;
+        float* dst = g.logits + ((size_t)buf * g.C + row) * g.Pp + n0;
+        float v[32];
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            v[j] = __uint_as_float(r[j]) + g.bias[n0 + j];
+            if (n0 + j < g.P) mx = fmaxf(mx, v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) *(float4*)(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (n0 + j < g.P) s += expf(v[j] - mx);
+        g.part[((size_t)buf * g.C + row) * g.NT + nt] = make_float2(mx, s);
+    }
+}
+
 __global__ void __launch_bounds__(128) k_learned_gemm(LGemmArgs g)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -313,43 +356,7 @@ __global__ void __launch_bounds__(128) k_learned_gemm(LGemmArgs g)
     tc_fence_after();
     const bool all_ok = __syncthreads_and(done_ok && *s_ok);
     if (all_ok) {
-        uint32_t r[32];
-        tc_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16), r);
-        tc_wait_ld();
-        const int row = mt * LR_TM + warp * 32 + lane;
-        const int n0 = nt * LR_TN;
-        if (g.mode == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = fmaxf(__uint_as_float(r[q * 8 + j]) + g.bias[n0 + q * 8 + j], 0.f);
-                uint4 o;
-                o.x = pack_bf16x2(v[0], v[1]);
-                o.y = pack_bf16x2(v[2], v[3]);
-                o.z = pack_bf16x2(v[4], v[5]);
-                o.w = pack_bf16x2(v[6], v[7]);
-                *(uint4*)(g.out_h + cm_off(row, n0 + q * 8, g.K, LR_TM)) = o;
-            }
-        } else if (row < g.C) {
-            const int cb = g.cur_buf[row];
-            const int buf = g.prime ? cb : 1 - cb;
-            float* dst = g.logits + ((size_t)buf * g.C + row) * g.Pp + n0;
-            float v[32];
-            float mx = -INFINITY;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                v[j] = __uint_as_float(r[j]) + g.bias[n0 + j];
-                if (n0 + j < g.P) mx = fmaxf(mx, v[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) *(float4*)(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            float s = 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (n0 + j < g.P) s += expf(v[j] - mx);
-            g.part[((size_t)buf * g.C + row) * g.NT + nt] = make_float2(mx, s);
-        }
+        lgemm_epilogue(g, tmem, warp, lane, mt, nt);
     } else if (tid == 0) {
         atomicOr(g.status, STATUS_TIMEOUT);
     }
@@ -400,25 +407,17 @@ __device__ __forceinline__ void load_z(const int32_t* row, int lane, int H, int3
     }
 }
 
-__global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, LearnArgs L, int flags)
+// One block's share of a learned MH step: warp w runs chain block * LR_WARPS + w; it
+// finishes the previous step (LF_FINISH) and starts the next (LF_START).  The survivors
+// are read from `sreg` once the staged copy has landed on `s_bar` (when `staged`), else
+// from global memory.  Thread 0 adds the block's re-scored items, and the last of the
+// `nblocks` blocks to finish advances the step counter.
+__device__ __forceinline__ void learned_chain_block(const ChainState& S, const LearnArgs& L, int flags, int block,
+                                                    int nblocks, const uint8_t* sreg, LWarp* sw, int64_t* s_items,
+                                                    uint64_t* s_bar, bool staged, bool stage_wait_at_end)
 {
-    extern __shared__ __align__(16) uint8_t sreg[];        // the survivors, staged
-    __shared__ LWarp sw[LR_WARPS];
-    __shared__ int64_t s_items[LR_WARPS];
-    __shared__ __align__(8) uint64_t s_bar;
-    const bool staged = L.sreg_bytes > 0;
-    if (threadIdx.x == 0 && staged) {
-        // the survivors do not change between launches: fetch them before the wait
-        mbar_init(&s_bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(&s_bar, L.sreg_bytes);
-        bulk_g2s(sreg, L.sreg, L.sreg_bytes, &s_bar, l2_policy_evict_last());
-    }
-    griddep_wait();
-    griddep_launch();
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * LR_WARPS + warp;
+    const int c = block * LR_WARPS + warp;
     const int n = S.n, H = L.H, NT = L.NT;
     const int64_t t_dev = *S.step;
     int64_t items = 0;
@@ -697,7 +696,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
             const int64_t* skey = L.skey;
             const uint32_t* srk = L.srk;
             const uint32_t* soff = L.soff;
-            if (staged && mbar_wait_bounded(&s_bar, 0, WAIT_TIMEOUT_NS)) {
+            if (staged && mbar_wait_bounded(s_bar, 0, WAIT_TIMEOUT_NS)) {
                 smask = (const uint64_t*)sreg;
                 skey = (const int64_t*)(sreg + L.so_key);
                 srk = (const uint32_t*)(sreg + L.so_rk);
@@ -774,7 +773,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
     if (lane == 0) s_items[warp] = items;
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (staged) mbar_wait_bounded(&s_bar, 0, WAIT_TIMEOUT_NS);     // no copy left in flight
+        if (staged && stage_wait_at_end) mbar_wait_bounded(s_bar, 0, WAIT_TIMEOUT_NS);   // no copy left in flight
         if (flags & LF_FINISH) {
             int64_t tot = 0;
             for (int w = 0; w < LR_WARPS; ++w) tot += s_items[w];
@@ -782,7 +781,7 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
             // the last block advances the step counter
             __threadfence();
             const uint32_t ticket = atomicAdd(L.done, 1u);
-            if (ticket == gridDim.x - 1) {
+            if (ticket == (uint32_t)nblocks - 1) {
                 const int64_t t_end = t_dev + 1;
                 *S.step = t_end;
                 if (S.record_every > 0 && t_end > S.burn_in) {
@@ -794,6 +793,195 @@ __global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, L
             }
         }
     }
+}
+
+
+__global__ void __launch_bounds__(32 * LR_WARPS) k_learned_chain(ChainState S, LearnArgs L, int flags)
+{
+    extern __shared__ __align__(16) uint8_t sreg[];        // the survivors, staged
+    __shared__ LWarp sw[LR_WARPS];
+    __shared__ int64_t s_items[LR_WARPS];
+    __shared__ __align__(8) uint64_t s_bar;
+    const bool staged = L.sreg_bytes > 0;
+    if (threadIdx.x == 0 && staged) {
+        // the survivors do not change between launches: fetch them before the wait
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&s_bar, L.sreg_bytes);
+        bulk_g2s(sreg, L.sreg, L.sreg_bytes, &s_bar, l2_policy_evict_last());
+    }
+    griddep_wait();
+    griddep_launch();
+    __syncthreads();
+    learned_chain_block(S, L, flags, blockIdx.x, gridDim.x, sreg, sw, s_items, &s_bar, staged, true);
+}
+
+// ---------------------------------------------------------------------------------
+// the persistent learned step
+// ---------------------------------------------------------------------------------
+// One cooperative launch runs many MH steps.  A step is three phases -- layer 2 on the
+// proposals' layer-1 outputs, the output layer, then the chains (finish the step, start
+// the next) -- separated by grid-wide barriers instead of kernel boundaries.  Every CTA
+// keeps its layer-2 or output-layer weight tile in shared memory and its TMEM columns for
+// the whole launch, and the chain CTAs keep the survivors staged; only the activations
+// and the chains' outputs pass through L2.  CTAs [0, n3) own output-layer tiles, CTAs
+// [n3, n3 + n2) layer-2 tiles, and CTAs [0, nc) four chains each.
+struct PersistArgs {
+    int iters;
+    int n2, n3, nc;
+    int nt2, nt3;                 // N tiles of layer 2 (H / 32) and of the output layer (NT)
+    uint32_t* gsync;              // grid barrier counter, zero at launch
+    uint32_t a_off, b_off, bar_off;   // dynamic shared memory: A tile, B tile, barriers
+    int staged;                   // chain CTAs stage the survivors at [0, L.sreg_bytes)
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// grid-wide barrier number k (1, 2, ...) of the launch: every CTA's writes before it are
+// visible after it, to generic loads and to the bulk copies (async proxy) issued after
+// it.  Bounded: false once the wait has run out (status gets STATUS_TIMEOUT).
+__device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t target, uint32_t* status, int* s_ok)
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        bool ok = true;
+        if (ld_acquire_gpu(counter) < target) {
+            const uint64_t t0 = global_timer_ns();
+            while (ld_acquire_gpu(counter) < target) {
+                if (global_timer_ns() - t0 > WAIT_TIMEOUT_NS) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (!ok) atomicOr(status, STATUS_TIMEOUT);
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// one GEMM tile of a phase: A (128 rows x K) by bulk copies, one mbarrier per 64-wide K
+// block (phase `parity`), MMAs into `tmem` as the blocks land, commit, epilogue
+__device__ __forceinline__ bool persist_gemm(const LGemmArgs& g, int mt, int nt, uint8_t* sA, const uint8_t* sB,
+                                             uint64_t* bar, uint32_t parity, uint32_t tmem, int* s_okg)
+{
+    const int KB = g.K >> 6, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        *s_okg = 1;
+        const uint64_t pol = l2_policy_evict_last();
+        const uint8_t* gA = g.A + (size_t)mt * LR_TM * g.K * 2;
+        for (int kb = 0; kb < KB; ++kb) {
+            mbar_arrive_expect_tx(&bar[kb], LR_TM * 128);
+            bulk_g2s(sA + (size_t)kb * LR_TM * 128, gA + (size_t)kb * LR_TM * 128, LR_TM * 128, &bar[kb], pol);
+        }
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            ok = mbar_wait_bounded(&bar[kb], parity, WAIT_TIMEOUT_NS);
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = tc_smem_desc(sA + (size_t)kb * LR_TM * 128 + kk * 256, 128, 1024);
+                const uint64_t bd = tc_smem_desc(sB + (size_t)kb * LR_TN * 128 + kk * 256, 128, 1024);
+                tc_mma_bf16(tmem, ad, bd, LR_IDESC, (kb | kk) != 0);
+            }
+        }
+        tc_commit(&bar[KB]);
+        if (!ok) {
+            *s_okg = 0;
+            for (int kb = 0; kb < KB; ++kb) mbar_wait_bounded(&bar[kb], parity, WAIT_TIMEOUT_NS);
+        }
+    }
+    __syncthreads();
+    const bool done_ok = mbar_wait_bounded(&bar[KB], parity, WAIT_TIMEOUT_NS);
+    tc_fence_after();
+    const bool all_ok = __syncthreads_and(done_ok && *s_okg);
+    if (all_ok) lgemm_epilogue(g, tmem, warp, lane, mt, nt);
+    else if (tid == 0) atomicOr(g.status, STATUS_TIMEOUT);
+    tc_fence_before();
+    return all_ok;
+}
+
+__global__ void __launch_bounds__(32 * LR_WARPS, 1)
+    k_learned_persist(ChainState S, LearnArgs L, LGemmArgs g2, LGemmArgs g3, PersistArgs P)
+{
+    extern __shared__ __align__(1024) uint8_t psm_raw[];
+    uint8_t* psm = (uint8_t*)(((uintptr_t)psm_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ LWarp sw[LR_WARPS];
+    __shared__ int64_t s_items[LR_WARPS];
+    __shared__ uint32_t s_tslot;
+    __shared__ int s_okg, s_okb;                       // GEMM and grid-barrier outcomes
+    const int cta = blockIdx.x, tid = threadIdx.x;
+    const bool is3 = cta < P.n3, is2 = !is3 && cta < P.n3 + P.n2, isc = cta < P.nc;
+    const bool gemm = is3 || is2;
+    const LGemmArgs& g = is3 ? g3 : g2;
+    const int tile = is3 ? cta : cta - P.n3;
+    const int ntiles = is3 ? P.nt3 : P.nt2;
+    const int mt = gemm ? tile / ntiles : 0, nt = gemm ? tile - mt * ntiles : 0;
+    const int KB = g2.K >> 6;
+    uint8_t* sA = psm + P.a_off;
+    uint8_t* sB = psm + P.b_off;
+    uint64_t* bar = (uint64_t*)(psm + P.bar_off);      // [KB] A blocks, [KB] commit, [KB+1] B, [KB+2] survivors
+    const bool staged = isc && P.staged;
+    if (gemm && tid < 32) {
+        tc_alloc(&s_tslot, 32);
+        tc_relinquish();
+    }
+    if (tid == 0) {
+        for (int kb = 0; kb < KB + 3; ++kb) mbar_init(&bar[kb], 1);
+        fence_mbar_init();
+        if (gemm) {
+            // the CTA's weight tile, resident for the launch
+            const uint8_t* gB = g.B + (size_t)nt * LR_TN * g.K * 2;
+            mbar_arrive_expect_tx(&bar[KB + 1], (uint32_t)(KB * LR_TN * 128));
+            for (int kb = 0; kb < KB; ++kb)
+                bulk_g2s(sB + (size_t)kb * LR_TN * 128, gB + (size_t)kb * LR_TN * 128, LR_TN * 128, &bar[KB + 1],
+                         l2_policy_evict_last());
+        }
+        if (staged) {
+            mbar_arrive_expect_tx(&bar[KB + 2], L.sreg_bytes);
+            bulk_g2s(psm, L.sreg, L.sreg_bytes, &bar[KB + 2], l2_policy_evict_last());
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tslot;
+    bool ok = true;
+    if (gemm) ok = mbar_wait_bounded(&bar[KB + 1], 0, WAIT_TIMEOUT_NS);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(g2.status, STATUS_TIMEOUT);
+    } else {
+        const uint32_t G = (uint32_t)gridDim.x;
+        uint32_t nb = 0;                                // barriers passed
+        for (int it = 0; it < P.iters; ++it) {
+            const uint32_t parity = (uint32_t)(it & 1);
+            if (is2 && !persist_gemm(g2, mt, nt, sA, sB, bar, parity, tmem, &s_okg)) ok = false;
+            if (!grid_barrier(P.gsync, G * ++nb, g2.status, &s_okb) || !ok) break;
+            if (is3 && !persist_gemm(g3, mt, nt, sA, sB, bar, parity, tmem, &s_okg)) ok = false;
+            if (!grid_barrier(P.gsync, G * ++nb, g2.status, &s_okb) || !ok) break;
+            if (isc)
+                learned_chain_block(S, L, LF_FINISH | LF_START, cta, P.nc, psm, sw, s_items, &bar[KB + 2], staged,
+                                    false);
+            if (it + 1 < P.iters && !grid_barrier(P.gsync, G * ++nb, g2.status, &s_okb)) break;
+        }
+    }
+    if (tid == 0 && staged) mbar_wait_bounded(&bar[KB + 2], 0, WAIT_TIMEOUT_NS);   // no copy left in flight
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (gemm && tid < 32) tc_dealloc(tmem, 32);
 }
 
 // current logits of every chain (row stride P)
@@ -823,6 +1011,10 @@ struct LearnedPath {
     bool primed = false;
     bool pdl = true;
     cudaGraphExec_t exec = nullptr;
+    uint32_t* gsync = nullptr;           // grid barrier counter of the persistent launch
+    int persist = -1;                    // persistent launch: -1 not checked, 0 no, 1 yes
+    PersistArgs pa{};
+    size_t persist_smem = 0;
 };
 
 }  // namespace bn
@@ -891,7 +1083,7 @@ static int learned_alloc(bn_chains* ch)
                  o_lg = take(4 * 2 * Cs * Pp), o_part = take(8 * 2 * Cs * lp->NT), o_cb = take(Cs),
                  o_since = take(8 * Cs * n), o_prank = take(4 * Cs * n), o_pkey = take(8 * Cs * n), o_pab = take(2 * Cs),
                  o_pair = take(4 * Cs), o_lqf = take(4 * Cs), o_pu = take(8 * Cs), o_dp = take(8 * Cs),
-                 o_done = take(4), o_bound = take(4), o_status = take(4);
+                 o_done = take(4), o_bound = take(4), o_status = take(4), o_gsync = take(4);
     // survivors region [masks | keys | ranks | node offsets], each part 16-byte aligned
     const size_t r_key = (size_t)round_up((int64_t)(8 * alive), 16), r_rk = r_key + (size_t)round_up((int64_t)(8 * alive), 16),
                  r_off = r_rk + (size_t)round_up((int64_t)(4 * alive), 16),
@@ -943,6 +1135,7 @@ static int learned_alloc(bn_chains* ch)
     lp->h2 = B + o_h2;
     lp->bound = (uint32_t*)(B + o_bound);
     lp->status = (uint32_t*)(B + o_status);
+    lp->gsync = (uint32_t*)(B + o_gsync);
     ch->lp = lp;
     return BN_OK;
 }
@@ -1122,6 +1315,83 @@ static int learned_graph(bn_chains* ch, cudaStream_t s)
     return set_error(BN_ECUDA, "learned proposal: graph capture failed");
 }
 
+// the persistent launch's plan: CTAs per role, shared-memory layout, and whether every
+// CTA can be resident at once (a cooperative launch needs that)
+static int persist_setup(bn_chains* ch)
+{
+    LearnedPath* lp = ch->lp;
+    if (lp->persist >= 0) return BN_OK;
+    lp->persist = 0;
+    PersistArgs& P = lp->pa;
+    P.nt2 = lp->H / LR_TN;
+    P.nt3 = lp->NT;
+    P.n2 = P.nt2 * lp->Mt;
+    P.n3 = P.nt3 * lp->Mt;
+    P.nc = (lp->C + LR_WARPS - 1) / LR_WARPS;
+    P.gsync = lp->gsync;
+    const size_t sreg = lp->L.sreg_bytes;
+    const size_t a_bytes = (size_t)LR_TM * lp->H * 2, b_bytes = (size_t)LR_TN * lp->H * 2;
+    const size_t bars = 8 * (size_t)(lp->H / 64 + 3);
+    const int dev = device_id();
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return BN_OK;
+    }
+    const size_t static_smem = sizeof(LWarp) * LR_WARPS + 64 + 1024;   // + alignment slack
+    auto layout = [&](bool stage) {
+        P.staged = stage ? 1 : 0;
+        const size_t a = stage ? (size_t)round_up((int64_t)sreg, 1024) : 0;
+        P.a_off = (uint32_t)a;
+        P.b_off = (uint32_t)(a + a_bytes);
+        P.bar_off = (uint32_t)(a + a_bytes + b_bytes);
+        return a + a_bytes + b_bytes + bars + 1024;
+    };
+    size_t smem = layout(sreg > 0);
+    if (smem + static_smem > (size_t)optin) smem = layout(false);     // survivors from global memory
+    if (smem + static_smem > (size_t)optin) return BN_OK;
+    if (cudaFuncSetAttribute(k_learned_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return BN_OK;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_learned_persist, 32 * LR_WARPS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return BN_OK;
+    }
+    const int grid = std::max(P.n2 + P.n3, P.nc);
+    if ((int64_t)per_sm * sm_count() < grid) return BN_OK;
+    lp->persist_smem = smem;
+    lp->persist = 1;
+    return BN_OK;
+}
+
+// `iters` learned steps (each: layer 2, output layer, finish + start) in one cooperative
+// launch
+static int launch_persist(bn_chains* ch, int iters, cudaStream_t s)
+{
+    LearnedPath* lp = ch->lp;
+    PersistArgs P = lp->pa;
+    P.iters = iters;
+    BN_CUDA(cudaMemsetAsync(lp->gsync, 0, sizeof(uint32_t), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max(P.n2 + P.n3, P.nc), 1, 1);
+    cfg.blockDim = dim3(32 * LR_WARPS, 1, 1);
+    cfg.dynamicSmemBytes = lp->persist_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BN_CUDA(cudaLaunchKernelEx(&cfg, k_learned_persist, ch->S, lp->L, lp->g2, lp->g3, P));
+    BN_LAUNCH_CHECK("k_learned_persist");
+    return BN_OK;
+}
+
+static constexpr int LR_PERSIST_ITERS = 256;   // learned steps per persistent launch
+
 int bn::learned_step(bn_chains* ch, int64_t steps, cudaStream_t s)
 {
     int rc = learned_setup(ch, s);
@@ -1129,6 +1399,14 @@ int bn::learned_step(bn_chains* ch, int64_t steps, cudaStream_t s)
     if (steps <= 0) return BN_OK;
     if ((rc = launch_chain(ch, LF_START, s))) return rc;
     int64_t mid = steps - 1;
+    if (ch->learned_launch == BN_LEARNED_LAUNCH_AUTO && mid > 0 && (rc = persist_setup(ch))) return rc;
+    if (ch->learned_launch == BN_LEARNED_LAUNCH_AUTO && ch->lp->persist == 1) {
+        for (; mid > 0;) {
+            const int k = (int)std::min<int64_t>(mid, LR_PERSIST_ITERS);
+            if ((rc = launch_persist(ch, k, s))) return rc;
+            mid -= k;
+        }
+    }
     if (mid >= LR_GRAPH_ITERS) {
         if ((rc = learned_graph(ch, s))) return rc;
         for (; mid >= LR_GRAPH_ITERS; mid -= LR_GRAPH_ITERS) {

@@ -1649,6 +1649,15 @@ static void default_mlp_weights(int n, int d, int H, uint64_t seed, std::vector<
     }
 }
 
+extern "C" int bn_chains_set_learned_launch(bn_chains* ch, int mode)
+{
+    set_error(BN_OK, "");
+    if (!ch || (mode != BN_LEARNED_LAUNCH_AUTO && mode != BN_LEARNED_LAUNCH_GRAPH))
+        return set_error(BN_EINVAL, "bn_chains_set_learned_launch: bad arguments");
+    ch->learned_launch = mode;
+    return BN_OK;
+}
+
 extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,
                            uint8_t* best_dag, double* best_score, double* edge_freq, bn_mcmc_stats* stats,
                            void* stream)

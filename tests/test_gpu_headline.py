@@ -134,3 +134,23 @@ def test_n60_headline_launches_equal_full_table_and_oracle(gpu, oracle_n60):
     # edge counts: every post-burn-in step counts each edge of the current greedy DAG once
     E = gpu.chains_read(fused, "edge_counts")
     assert (E.sum((1, 2)) <= 2000 * n * k).all() and (np.diagonal(E, axis1=1, axis2=2) == 0).all()
+
+
+@pytest.mark.parametrize("B", [4, 8, 1024])
+def test_n60_batched_scoring_against_oracle(gpu, oracle_n60, B):
+    """bn_score_orders at the bench's table on the oracle's entries: the few-order scan
+    (B = 4), the full-table scan (B = 8, 1,024; autotuned tiling) and the pruned table
+    give the same ranks and FP64 sums, and a sample of orders equals the oracle's
+    brute-force order score."""
+    _, _, k, _, tab = oracle_n60
+    orders = synth.random_orders(60, B, 1700 + B)
+    full = gpu.table_from_scores(tab, k)
+    br_f, sc_f = gpu.score_orders(full, orders)
+    pruned = gpu.table_from_scores(tab, k)
+    gpu.table_set_scan(pruned, gpu.SCAN_PRUNED)
+    br_p, sc_p = gpu.score_orders(pruned, orders)
+    assert np.array_equal(br_f, br_p) and np.array_equal(sc_f, sc_p)
+    pick = sorted(set([0, B - 1] + list(np.random.default_rng(B).choice(B, min(B, 14), replace=False))))
+    sc_ref, br_ref = oracle.order_scores(tab, k, orders[pick])
+    assert np.array_equal(br_f[pick], br_ref)
+    assert np.array_equal(sc_f[pick], sc_ref)

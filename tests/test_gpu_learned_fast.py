@@ -117,3 +117,32 @@ def test_uniform_steps_between_learned_calls(gpu):
     sc = gpu.chains_read(ch, "scores")
     for c in range(0, 64, 9):
         assert sc[c] == pytest.approx(oracle.order_score(tab, k, O[c])[0], rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("name,d,H,C,steps", [("n6_k2_m100", 8, 128, 37, 300), ("n20_k4_m1000", 32, 256, 200, 600),
+                                              ("n60_k4_m1000", 32, 512, 256, 300)])
+def test_persistent_launch_equals_graph_launch(gpu, name, d, H, C, steps):
+    """The persistent cooperative kernel (the three phases of each step separated by
+    grid-wide barriers, up to 256 steps per launch) gives bit for bit what the three
+    kernels per step replayed from a CUDA graph give: traces, states, best states, edge
+    counts, records and the network outputs held for the final orders."""
+    data, arity, k, R, _ = synth.workload(name)
+    n = data.shape[1]
+    t = gpu.build_scores(data, arity, k, R=R)
+    gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+    w, _ = _weights(n, d, H, 21, sharpen=4.0)
+    out = []
+    for mode in (gpu.LEARNED_LAUNCH_GRAPH, gpu.LEARNED_LAUNCH_AUTO):
+        net = gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=C)
+        ch = gpu.chains_create(t, C, 41, burn_in=50, trace_cap=steps, record_every=3, record_cap=steps)
+        gpu.chains_set_learned_launch(ch, mode)
+        gpu.chains_step(ch, 20)
+        gpu.chains_set_proposal(ch, net, gpu.PROPOSAL_LEARNED, eps_mix=0.15)
+        gpu.chains_step(ch, steps // 3)
+        gpu.chains_step(ch, steps - 20 - steps // 3)
+        out.append({what: gpu.chains_read(ch, what) for what in
+                    ("trace_score", "trace_accept", "orders", "scores", "ranks", "best_scores", "best_orders",
+                     "best_ranks", "accepts", "edge_counts", "steps", "items", "record", "record_len", "logits")})
+    for what in out[0]:
+        assert np.array_equal(out[0][what], out[1][what]), what
+    assert out[1]["accepts"].sum() > 0
