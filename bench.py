@@ -365,6 +365,38 @@ def _batch_learned(bn, torch, synth, nets, tabs, seed, args):
     return out
 
 
+def _oracle_configs(synth, nt, configs):
+    """The oracle on all host cores at the other workloads: order evaluations/s on seeded
+    random orders (n = 20 and n = 40 tables it builds itself), table entries/s of its
+    build at n = 20, and the ESS/s its sampler would reach at n = 20: its trajectories are
+    the library's step for step (tested), so its ESS per step is the library's and its
+    ESS/s = that ESS x its steps/s."""
+    import oracle
+    out = {}
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t0 = time.perf_counter()
+    tab20 = oracle.build_table(data, arity, k, R=R, threads=nt)
+    el = time.perf_counter() - t0
+    out["n20_table_entries_per_s"] = tab20.size / el
+    for name, tab, B in (("n20", tab20, 1000), ("n40", None, 10 * nt)):
+        if tab is None:
+            rng = np.random.Generator(np.random.PCG64(0xB4E50002))
+            tab = rng.standard_normal((40, oracle.num_sets(39, 4))) * 10.0 - 500.0     # stand-in values
+        orders = synth.random_orders(tab.shape[0], B, 7)
+        t0 = time.perf_counter()
+        oracle.order_scores(tab, 4, orders, threads=nt)
+        el = time.perf_counter() - t0
+        out[f"{name}_order_evals_per_s"] = B / el
+    c20 = (configs or {}).get("n20_64chains") or {}
+    if c20.get("ess_median"):
+        per_step = c20["ess_median"] / 20000.0
+        out["n20_ess_per_s"] = per_step * out["n20_order_evals_per_s"] / 64.0
+    out["cores"] = nt
+    out["note"] = ("n20: the oracle's own table (prior included); n40: a stand-in table of the shape (timing does "
+                   "not depend on the values); 1,000 and 10 x cores orders")
+    return out
+
+
 def _config_n20(bn, torch, synth, seed):
     """20 ternary nodes, m = 1000, k = 4, with the pairwise prior (10 % of the true edges at
     +1, 10 % of the non-edges at -1); 64 chains x 20,000 iterations through the one-shot
@@ -566,6 +598,12 @@ def main():
         # the fused sampler kernel, launch by launch (up to 1024 iterations per launch)
         fused_ms, fused_l = bn.chains_step_profiled(chains, max(ips, 256) * 4, stream=stream.cuda_stream)
         chains.free()
+        # the same kernel with one chain: one warp alone on the GPU, nothing competing for
+        # its SM -- the dependent-latency floor of this code's MH step
+        solo = bn.chains_create(table, 1, seed=seed + 99)
+        bn.chains_step(solo, 2 * max(ips, 256), stream=stream.cuda_stream)
+        solo_ms, solo_l = bn.chains_step_profiled(solo, max(ips, 256) * 4, stream=stream.cuda_stream)
+        solo.free()
 
     # ---- bn_score_orders on the pruned table (only entries no subset matches or beats) -----
     pruned_scoring = []
@@ -690,6 +728,11 @@ def main():
                                     "warp_instructions": inst,
                                     "warp_instructions_per_chain_iteration": FUSED_INST_PER_CHAIN_STEP,
                                     "us_per_iteration": 1000.0 * avg_fused / iters_fused},
+                     "latency_floor": {"us_per_iteration_one_chain": 1000.0 * solo_ms / (max(ips, 256) * 4),
+                                       "frac": (solo_ms / (max(ips, 256) * 4)) / (avg_fused / iters_fused),
+                                       "note": "the same kernel and table with a single chain (one warp alone on "
+                                               "the GPU): the dependent-latency floor of this MH step's code; frac = "
+                                               "floor / the 256-chain time per iteration"},
                      "note": "latency-bound: 256 chains are 256 warps on 152 SMs, and each warp's MH step is a "
                              "chain of dependent shared-memory loads, shuffles and votes, so issue slots stay "
                              "idle; the instruction count per chain-iteration is ncu's smsp__inst_executed.sum "
@@ -721,6 +764,7 @@ def main():
             rate1, done1, el1, _ = oracle_sample(args.cpu_seconds / 2, threads=1)
             cpu1 = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
                     "sample": f"{done1} order evaluations ({el1:.1f} s), one thread"}
+            cpu["configs"] = _oracle_configs(synth, nt, configs)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -771,6 +815,7 @@ def main():
             "clocks": clocks,
             "table_build_s": build_s,
             "table_entries_per_s": n * S / build_s,
+            "table_row_visits_per_s": n * S * data.shape[0] / build_s,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -329,6 +329,20 @@ int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps,
                 uint8_t* best_order, uint8_t* best_dag, double* best_score,
                 double* edge_freq, bn_mcmc_stats* stats, void* stream);
 
+/* bn_mcmc_run for `count` networks of uneven size stepped together (the paper learns one
+ * network at a time): network i runs on tables[i] with params[i] (learned networks train
+ * first, on their own chains), then every network takes `steps` sampling steps in one
+ * batch (bn_batch_step: the uniform-proposal networks on pruned tables share one fused
+ * launch per 1,024 steps).  Outputs per network, any array or entry may be NULL:
+ * best_order[i] (n_i uint8), best_dag[i] (n_i x n_i), best_score[i], edge_freq[i]
+ * (n_i x n_i), stats[i] (sample_ms and train_ms are the whole batch's).  Each network's
+ * results equal its own bn_mcmc_run with the same parameters.  Errors: as bn_mcmc_run,
+ * naming the network. */
+int bn_mcmc_run_batch(int count, const bn_table* const* tables, const bn_mcmc_params* params,
+                      int64_t steps, uint8_t* const* best_order, uint8_t* const* best_dag,
+                      double* best_score, double* const* edge_freq, bn_mcmc_stats* stats,
+                      void* stream);
+
 /* Batches of networks of uneven size (the paper samples one network at a time): count
  * networks, each with its own table and chain parameters.  bn_batch_step advances every
  * network by `steps` MH steps; the networks whose chains use the uniform proposal on a

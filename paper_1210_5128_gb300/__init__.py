@@ -99,6 +99,7 @@ def _load():
     _L.bn_chains_free.restype = None
     _L.bn_mcmc_run.argtypes = [_vp, C.POINTER(MCMCParams), C.c_int64, _vp, _vp, _vp, _vp,
                                C.POINTER(MCMCStats), _vp]
+    _L.bn_mcmc_run_batch.argtypes = [C.c_int, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
     _L.bn_measure_test_rate.argtypes = [_vp, C.POINTER(C.c_double)]
     _L.bn_chains_set_learned_launch.argtypes = [_vp, C.c_int]
     _L.bn_mlp_create.argtypes = [C.c_int, C.POINTER(MLPParams)] + [_vp] * 7 + [C.c_int, _vp, C.POINTER(_vp)]
@@ -472,6 +473,30 @@ def mcmc_run(t: Table, chains, steps, seed, burn_in=0, literal_log=False, propos
                              None))
     stats = {f: getattr(st, f) for f, _ in MCMCStats._fields_}
     return dict(best_order=bo, best_dag=dag, best_score=float(bs[0]), edge_freq=ef, stats=stats)
+
+
+def mcmc_run_batch(tables, chains, steps, seeds, burn_in=0, thin=0, proposals=None, eps_mix=0.1,
+                   train_iters=0):
+    """bn_mcmc_run_batch: one-shot runs of many networks stepped together; ``chains`` and
+    ``seeds`` are ints or per-network lists, ``proposals`` None (uniform) or a list.
+    Returns one dict per network, as mcmc_run."""
+    cnt = len(tables)
+    chains = chains if hasattr(chains, "__len__") else [chains] * cnt
+    seeds = seeds if hasattr(seeds, "__len__") else [seeds + i for i in range(cnt)]
+    proposals = proposals or [PROPOSAL_UNIFORM] * cnt
+    ps = (MCMCParams * cnt)(*[MCMCParams(int(chains[i]), burn_in, int(seeds[i]), 0, 0, 0, 0, 0, int(proposals[i]),
+                                         eps_mix, train_iters, thin, None) for i in range(cnt)])
+    hs = (C.c_void_p * cnt)(*[t.handle for t in tables])
+    ns = [table_info(t)["n"] for t in tables]
+    bo = [np.empty(n, np.uint8) for n in ns]
+    dag = [np.empty((n, n), np.uint8) for n in ns]
+    ef = [np.empty((n, n), np.float64) for n in ns]
+    bs = np.empty(cnt, np.float64)
+    st = (MCMCStats * cnt)()
+    ptrs = lambda arrs: (C.c_void_p * cnt)(*[a.ctypes.data for a in arrs])      # noqa: E731
+    _check(lib().bn_mcmc_run_batch(cnt, hs, ps, steps, ptrs(bo), ptrs(dag), _ptr(bs), ptrs(ef), st, None))
+    return [dict(best_order=bo[i], best_dag=dag[i], best_score=float(bs[i]), edge_freq=ef[i],
+                 stats={f: getattr(st[i], f) for f, _ in MCMCStats._fields_}) for i in range(cnt)]
 
 
 # ---- learned proposal ----------------------------------------------------------------

@@ -1658,69 +1658,62 @@ extern "C" int bn_chains_set_learned_launch(bn_chains* ch, int mode)
     return BN_OK;
 }
 
-extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,
-                           uint8_t* best_dag, double* best_score, double* edge_freq, bn_mcmc_stats* stats,
-                           void* stream)
+// checks of the run-level fields of bn_mcmc_params (bn_mcmc_run, bn_mcmc_run_batch)
+static int run_params_check(const bn_table* t, const bn_mcmc_params* p, const char* who)
 {
-    set_error(BN_OK, "");
-    if (!t || !p || steps < 0) return set_error(BN_EINVAL, "bn_mcmc_run: bad arguments");
     const bool learned = p->proposal == BN_PROPOSAL_LEARNED;
     if (!learned && p->proposal != BN_PROPOSAL_UNIFORM)
-        return set_error(BN_EINVAL, "bn_mcmc_run: proposal %d (BN_PROPOSAL_UNIFORM or BN_PROPOSAL_LEARNED)",
-                         p->proposal);
+        return set_error(BN_EINVAL, "%s: proposal %d (BN_PROPOSAL_UNIFORM or BN_PROPOSAL_LEARNED)", who, p->proposal);
     if (learned && (!(p->eps_mix > 0.0 && p->eps_mix <= 1.0) || p->train_iters < 0))
-        return set_error(BN_EINVAL, "bn_mcmc_run: eps_mix in (0, 1] and train_iters >= 0 for the learned proposal");
-    if (p->thin < 0) return set_error(BN_EINVAL, "bn_mcmc_run: thin=%d", p->thin);
+        return set_error(BN_EINVAL, "%s: eps_mix in (0, 1] and train_iters >= 0 for the learned proposal", who);
+    if (p->thin < 0) return set_error(BN_EINVAL, "%s: thin=%d", who, p->thin);
     if (learned && p->net && (p->net->n != t->n || p->net->cap < p->chains))
-        return set_error(BN_EINVAL, "bn_mcmc_run: the network's n or batch_cap does not fit the run");
-    cudaStream_t s = (cudaStream_t)stream;
-    const int n = t->n, C = p->chains;
-    const int64_t train = learned ? p->train_iters : 0, total = train + steps;
+        return set_error(BN_EINVAL, "%s: the network's n or batch_cap does not fit the run", who);
+    return BN_OK;
+}
+
+// the chain parameters of a run: traces off, recording from `thin` over all its steps
+static bn_mcmc_params run_chain_params(const bn_mcmc_params* p, int64_t total)
+{
     bn_mcmc_params cp = *p;
     cp.trace = 0;
     cp.trace_cap = 0;
     cp.record_every = p->thin;
     cp.record_cap = p->thin > 0 ? (int)std::max<int64_t>(1, (total - p->burn_in + p->thin - 1) / p->thin) : 0;
-    bn_chains* ch = nullptr;
-    int rc = bn_chains_create(t, &cp, nullptr, BN_MEM_HOST, stream, &ch);
-    if (rc) return rc;
-    bn_mlp* own = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    struct G {
-        bn_chains* c;
-        bn_mlp** m;
-        cudaEvent_t* e;
-        ~G()
-        {
-            bn_chains_free(c);
-            bn_mlp_free(*m);
-            for (int i = 0; i < 3; ++i)
-                if (e[i]) cudaEventDestroy(e[i]);
-        }
-    } g{ch, &own, ev};
-    for (int i = 0; i < 3; ++i) BN_CUDA(cudaEventCreate(&ev[i]));
+    return cp;
+}
+
+// the learned proposal's set-up of a run: the caller's network or one created from the
+// seed (d = 32, H = 512), then train_iters training steps of the chains alone
+static int run_learned_setup(bn_chains* ch, const bn_mcmc_params* p, void* stream, bn_mlp** own)
+{
     bn_mlp* net = p->net;
-    if (learned && !net) {
-        const int d = 32, H = 512;
+    int rc;
+    if (!net) {
+        const int n = ch->S.n, d = 32, H = 512;
         std::vector<float> w[7];
         default_mlp_weights(n, d, H, p->seed, w);
-        bn_mlp_params mp = {d, H, C, 2e-3f, 0.f, 0.f, 0.f};
+        bn_mlp_params mp = {d, H, p->chains, 2e-3f, 0.f, 0.f, 0.f};
         if ((rc = bn_mlp_create(n, &mp, w[0].data(), w[1].data(), w[2].data(), w[3].data(), w[4].data(),
-                                w[5].data(), w[6].data(), BN_MEM_HOST, stream, &own)))
+                                w[5].data(), w[6].data(), BN_MEM_HOST, stream, own)))
             return rc;
-        net = own;
+        net = *own;
     }
-    BN_CUDA(cudaEventRecord(ev[0], s));
-    if (learned) {
-        if ((rc = bn_chains_set_proposal(ch, net, BN_PROPOSAL_TRAIN, p->eps_mix, stream))) return rc;
-        if ((rc = bn_chains_step(ch, train, stream))) return rc;
-        if ((rc = bn_chains_set_proposal(ch, net, BN_PROPOSAL_LEARNED, p->eps_mix, stream))) return rc;
-    }
-    std::vector<int64_t> acc0(C), acc1(C);
-    if (stats) BN_CUDA(cudaMemcpyAsync(acc0.data(), ch->S.accepts, 8 * (size_t)C, cudaMemcpyDeviceToHost, s));
-    BN_CUDA(cudaEventRecord(ev[1], s));
-    if ((rc = bn_chains_step(ch, steps, stream))) return rc;
-    BN_CUDA(cudaEventRecord(ev[2], s));
+    if ((rc = bn_chains_set_proposal(ch, net, BN_PROPOSAL_TRAIN, p->eps_mix, stream))) return rc;
+    if ((rc = bn_chains_step(ch, p->train_iters, stream))) return rc;
+    return bn_chains_set_proposal(ch, net, BN_PROPOSAL_LEARNED, p->eps_mix, stream);
+}
+
+// a run's outputs from its chains: the best state over all chains and its greedy DAG,
+// edge frequencies over the post-burn-in steps, and the summary (acc0: the chains'
+// accept counters before the sampling steps)
+static int run_collect(bn_chains* ch, const bn_mcmc_params* p, int64_t total, int64_t steps,
+                       const std::vector<int64_t>& acc0, double sample_ms, double train_ms, uint8_t* best_order,
+                       uint8_t* best_dag, double* best_score, double* edge_freq, bn_mcmc_stats* stats, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const bn_table* t = ch->t;
+    const int n = t->n, C = p->chains;
     uint8_t *d_o = nullptr, *d_dag = nullptr;
     double *d_s = nullptr, *d_f = nullptr;
     BN_CUDA(cudaMallocAsync((void**)&d_o, n, s));
@@ -1733,6 +1726,7 @@ extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t s
     k_edge_freq<<<(n * n + 127) / 128, 128, 0, s>>>(ch->S.edge, C, n, denom, d_f);
     BN_LAUNCH_CHECK("k_edge_freq");
     std::vector<double> f((size_t)n * n);
+    std::vector<int64_t> acc1(C);
     if (best_order) BN_CUDA(cudaMemcpyAsync(best_order, d_o, n, cudaMemcpyDeviceToHost, s));
     if (best_dag) BN_CUDA(cudaMemcpyAsync(best_dag, d_dag, (size_t)n * n, cudaMemcpyDeviceToHost, s));
     if (best_score) BN_CUDA(cudaMemcpyAsync(best_score, d_s, 8, cudaMemcpyDeviceToHost, s));
@@ -1749,17 +1743,15 @@ extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t s
         int64_t acc = 0;
         for (int c = 0; c < C; ++c) acc += acc1[c] - acc0[c];
         st.acceptance = steps > 0 ? (double)acc / ((double)C * (double)steps) : 0.0;
-        float ms = 0.f;
-        BN_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-        st.train_ms = learned ? ms : 0.0;
-        BN_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
-        st.sample_ms = ms;
+        st.train_ms = train_ms;
+        st.sample_ms = sample_ms;
         st.order_evals = (int64_t)C * total;
         st.ess_median = st.ess_min = std::nan("");
         st.uncertain_edges = 0;
         if (p->thin > 0) {
             std::vector<double> ess((size_t)n * n);
-            if ((rc = bn_chains_read(ch, BN_OUT_ESS, ess.data(), BN_MEM_HOST, stream))) return rc;
+            int rc = bn_chains_read(ch, BN_OUT_ESS, ess.data(), BN_MEM_HOST, stream);
+            if (rc) return rc;
             std::vector<double> unc;
             for (size_t e = 0; e < ess.size(); ++e)
                 if (f[e] >= 0.05 && f[e] <= 0.95 && !std::isnan(ess[e])) unc.push_back(ess[e]);
@@ -1774,6 +1766,65 @@ extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t s
         *stats = st;
     }
     return BN_OK;
+}
+
+struct RunEvents {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~RunEvents()
+    {
+        for (int i = 0; i < 3; ++i)
+            if (e[i]) cudaEventDestroy(e[i]);
+    }
+    int create()
+    {
+        for (int i = 0; i < 3; ++i) BN_CUDA(cudaEventCreate(&e[i]));
+        return BN_OK;
+    }
+    double ms(int a, int b) const
+    {
+        float v = 0.f;
+        cudaEventElapsedTime(&v, e[a], e[b]);
+        return v;
+    }
+};
+
+extern "C" int bn_mcmc_run(const bn_table* t, const bn_mcmc_params* p, int64_t steps, uint8_t* best_order,
+                           uint8_t* best_dag, double* best_score, double* edge_freq, bn_mcmc_stats* stats,
+                           void* stream)
+{
+    set_error(BN_OK, "");
+    if (!t || !p || steps < 0) return set_error(BN_EINVAL, "bn_mcmc_run: bad arguments");
+    int rc = run_params_check(t, p, "bn_mcmc_run");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool learned = p->proposal == BN_PROPOSAL_LEARNED;
+    const int C = p->chains;
+    const int64_t total = (learned ? p->train_iters : 0) + steps;
+    const bn_mcmc_params cp = run_chain_params(p, total);
+    bn_chains* ch = nullptr;
+    if ((rc = bn_chains_create(t, &cp, nullptr, BN_MEM_HOST, stream, &ch))) return rc;
+    bn_mlp* own = nullptr;
+    RunEvents ev;
+    struct G {
+        bn_chains* c;
+        bn_mlp** m;
+        ~G()
+        {
+            bn_chains_free(c);
+            bn_mlp_free(*m);
+        }
+    } g{ch, &own};
+    if ((rc = ev.create())) return rc;
+    BN_CUDA(cudaEventRecord(ev.e[0], s));
+    if (learned && (rc = run_learned_setup(ch, p, stream, &own))) return rc;
+    std::vector<int64_t> acc0(C);
+    if (stats) BN_CUDA(cudaMemcpyAsync(acc0.data(), ch->S.accepts, 8 * (size_t)C, cudaMemcpyDeviceToHost, s));
+    BN_CUDA(cudaEventRecord(ev.e[1], s));
+    if ((rc = bn_chains_step(ch, steps, stream))) return rc;
+    BN_CUDA(cudaEventRecord(ev.e[2], s));
+    BN_CUDA(cudaEventSynchronize(ev.e[2]));
+    return run_collect(ch, p, total, steps, acc0, ev.ms(1, 2), learned ? ev.ms(0, 1) : 0.0, best_order, best_dag,
+                       best_score, edge_freq, stats, stream);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1922,4 +1973,65 @@ extern "C" void bn_batch_free(bn_batch* b)
     for (bn_chains* c : b->chains) bn_chains_free(c);
     cudaFree(b->dev);
     delete b;
+}
+
+extern "C" int bn_mcmc_run_batch(int count, const bn_table* const* tables, const bn_mcmc_params* params,
+                                 int64_t steps, uint8_t* const* best_order, uint8_t* const* best_dag,
+                                 double* best_score, double* const* edge_freq, bn_mcmc_stats* stats, void* stream)
+{
+    set_error(BN_OK, "");
+    if (count < 1 || !tables || !params || steps < 0) return set_error(BN_EINVAL, "bn_mcmc_run_batch: bad arguments");
+    int rc;
+    for (int i = 0; i < count; ++i) {
+        if (!tables[i]) return set_error(BN_EINVAL, "bn_mcmc_run_batch: network %d has no table", i);
+        if ((rc = run_params_check(tables[i], &params[i], "bn_mcmc_run_batch"))) return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<bn_mcmc_params> cps(count);
+    std::vector<int64_t> total(count);
+    for (int i = 0; i < count; ++i) {
+        const bool learned = params[i].proposal == BN_PROPOSAL_LEARNED;
+        total[i] = (learned ? params[i].train_iters : 0) + steps;
+        cps[i] = run_chain_params(&params[i], total[i]);
+    }
+    bn_batch* b = nullptr;
+    if ((rc = bn_batch_create(count, tables, cps.data(), stream, &b))) return rc;
+    std::vector<bn_mlp*> own(count, nullptr);
+    struct G {
+        bn_batch* b;
+        std::vector<bn_mlp*>& m;
+        ~G()
+        {
+            bn_batch_free(b);
+            for (bn_mlp* x : m) bn_mlp_free(x);
+        }
+    } g{b, own};
+    RunEvents ev;
+    if ((rc = ev.create())) return rc;
+    BN_CUDA(cudaEventRecord(ev.e[0], s));
+    for (int i = 0; i < count; ++i)
+        if (params[i].proposal == BN_PROPOSAL_LEARNED &&
+            (rc = run_learned_setup(b->chains[i], &params[i], stream, &own[i])))
+            return rc;
+    std::vector<std::vector<int64_t>> acc0(count);
+    for (int i = 0; i < count; ++i) {
+        acc0[i].resize(params[i].chains);
+        if (stats)
+            BN_CUDA(cudaMemcpyAsync(acc0[i].data(), b->chains[i]->S.accepts, 8 * (size_t)params[i].chains,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    BN_CUDA(cudaEventRecord(ev.e[1], s));
+    if ((rc = bn_batch_step(b, steps, stream))) return rc;
+    BN_CUDA(cudaEventRecord(ev.e[2], s));
+    BN_CUDA(cudaEventSynchronize(ev.e[2]));
+    const double sample_ms = ev.ms(1, 2), train_ms = ev.ms(0, 1);
+    for (int i = 0; i < count; ++i) {
+        const bool learned = params[i].proposal == BN_PROPOSAL_LEARNED;
+        if ((rc = run_collect(b->chains[i], &params[i], total[i], steps, acc0[i], sample_ms, learned ? train_ms : 0.0,
+                              best_order ? best_order[i] : nullptr, best_dag ? best_dag[i] : nullptr,
+                              best_score ? &best_score[i] : nullptr, edge_freq ? edge_freq[i] : nullptr,
+                              stats ? &stats[i] : nullptr, stream)))
+            return rc;
+    }
+    return BN_OK;
 }

@@ -155,3 +155,29 @@ def test_batch_with_learned_networks_equals_networks_alone(gpu):
         for what in OUTS:
             assert np.array_equal(gpu.chains_read(b.chains(i), what), gpu.chains_read(alone, what)), (i, what)
         assert gpu.chains_read(b.chains(i), "accepts").max() > 0
+
+
+def test_mcmc_run_batch_equals_single_runs(gpu):
+    """bn_mcmc_run_batch: every network's one-shot results (best state, DAG, edge
+    frequencies, acceptance and ESS) equal its own bn_mcmc_run with the same parameters,
+    uniform and learned networks mixed."""
+    nets = _nets(4, 13)
+    tables = []
+    for data, ar, k in nets:
+        t = gpu.build_scores(data, ar, k)
+        gpu.table_set_scan(t, gpu.SCAN_PRUNED)
+        tables.append(t)
+    chains, seeds = [16, 8, 32, 4], [3, 4, 5, 6]
+    props = [gpu.PROPOSAL_UNIFORM, gpu.PROPOSAL_LEARNED, gpu.PROPOSAL_UNIFORM, gpu.PROPOSAL_UNIFORM]
+    out = gpu.mcmc_run_batch(tables, chains, 400, seeds, burn_in=40, thin=2, proposals=props, eps_mix=0.2,
+                             train_iters=60)
+    for i, t in enumerate(tables):
+        one = gpu.mcmc_run(t, chains[i], 400, seed=seeds[i], burn_in=40, thin=2, proposal=props[i], eps_mix=0.2,
+                           train_iters=60)
+        for key in ("best_order", "best_dag", "edge_freq"):
+            assert np.array_equal(out[i][key], one[key]), (i, key)
+        assert out[i]["best_score"] == one["best_score"]
+        for key in ("acceptance", "uncertain_edges", "order_evals"):
+            assert out[i]["stats"][key] == one["stats"][key], (i, key)
+        a, b = out[i]["stats"]["ess_median"], one["stats"]["ess_median"]
+        assert (np.isnan(a) and np.isnan(b)) or a == b
