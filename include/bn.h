@@ -79,6 +79,14 @@ int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int
                     const double* R, const bn_score_params* params, int mem,
                     void* stream, bn_table** out);
 
+/* bn_build_scores with the device time of its counting-and-scoring kernel (the table
+ * build of Eq. (3)-(4), the call's dominant launch) measured by CUDA events on `stream`
+ * around that launch: *build_ms receives it (build_ms may be NULL).  Outputs and errors as
+ * bn_build_scores. */
+int bn_build_scores_profiled(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                             const double* R, const bn_score_params* params, int mem,
+                             void* stream, bn_table** out, double* build_ms);
+
 /* bn_build_scores for `count` networks of uneven size in one call (many-network batches,
  * the paper learns one network at a time): network i has data[i] (m[i] x n[i]), arity[i],
  * k[i], R[i] (R may be NULL, or R[i] NULL: no prior) and params[i] (params may be NULL:

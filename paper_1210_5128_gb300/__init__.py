@@ -78,6 +78,8 @@ def _load():
     _L.bn_build_scores.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, C.POINTER(ScoreParams),
                                    C.c_int, _vp, C.POINTER(_vp)]
     _L.bn_table_from_scores.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]
+    _L.bn_build_scores_profiled.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int, _vp, C.POINTER(ScoreParams),
+                                            C.c_int, _vp, C.POINTER(_vp), C.POINTER(C.c_double)]
     _L.bn_build_scores_batch.argtypes = [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp, _vp]
     _L.bn_table_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]
@@ -233,6 +235,20 @@ def build_scores(data, arity, k, R=None, score_kind=0, ess=1.0, log10_gamma=0.0)
         _check(lib().bn_build_scores(_ptr(d), m, n, _ptr(a), k, _ptr(r), C.byref(p), MEM_HOST,
                                   None, C.byref(h)))
     return Table(h)
+
+
+def build_scores_profiled(data, arity, k, R=None, score_kind=0, ess=1.0, log10_gamma=0.0):
+    """bn_build_scores_profiled on host arrays: (table, device ms of the build kernel)."""
+    p = ScoreParams(score_kind, ess, log10_gamma)
+    h = _vp()
+    d = _host(data, np.uint8)
+    a = _host(arity, np.uint8)
+    r = _host(R, np.float64) if R is not None else None
+    m, n = d.shape
+    ms = C.c_double()
+    _check(lib().bn_build_scores_profiled(_ptr(d), m, n, _ptr(a), k, _ptr(r), C.byref(p), MEM_HOST, None,
+                                          C.byref(h), C.byref(ms)))
+    return Table(h), ms.value
 
 
 def build_scores_batch(nets, score_kind=0, ess=1.0, log10_gamma=0.0):

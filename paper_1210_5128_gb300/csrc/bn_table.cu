@@ -585,7 +585,8 @@ static int build_plan(const uint8_t* data, int m, int n, const uint8_t* arity, i
 // Device half: every kernel of the build on stream s, writing t (allocated) and OR-ing
 // STATUS_BADINPUT into *d_status for a data value at or above its arity.  Temporaries
 // are stream-ordered; nothing here waits for the device.
-static int build_enqueue(const BuildPlan& P, bn_table* t, uint32_t* d_status, cudaStream_t s)
+static int build_enqueue(const BuildPlan& P, bn_table* t, uint32_t* d_status, cudaStream_t s,
+                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
     const int n = P.n, m = P.m, k = P.k;
     const std::vector<double>& alpha = P.alpha;
@@ -656,6 +657,7 @@ static int build_enqueue(const BuildPlan& P, bn_table* t, uint32_t* d_status, cu
     int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, (units + nwarps - 1) / nwarps);
     if (grid < 1) grid = 1;
     int kt = k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 12;
+    if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
     switch (kt) {
         case 2: rc = launch_build_kt<2>(A, smem_data, smem, grid, s); break;
         case 4: rc = launch_build_kt<4>(A, smem_data, smem, grid, s); break;
@@ -663,12 +665,13 @@ static int build_enqueue(const BuildPlan& P, bn_table* t, uint32_t* d_status, cu
         default: rc = launch_build_kt<12>(A, smem_data, smem, grid, s); break;
     }
     if (rc) return rc;
+    if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     return rank_entries(t, s);
 }
 
-extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
-                               const double* R, const bn_score_params* params, int mem,
-                               void* stream, bn_table** out)
+static int build_scores_impl(const uint8_t* data, int m, int n, const uint8_t* arity, int k, const double* R,
+                             const bn_score_params* params, int mem, void* stream, bn_table** out,
+                             cudaEvent_t ev0, cudaEvent_t ev1)
 {
     set_error(BN_OK, "");
     if (!out) return set_error(BN_EINVAL, "bn_build_scores: out is NULL");
@@ -692,7 +695,7 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
         Temps tmp(s);
         if ((rc = tmp.get(&d_status, 1))) return rc;
         BN_CUDA(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
-        if ((rc = build_enqueue(P, t, d_status, s))) return rc;
+        if ((rc = build_enqueue(P, t, d_status, s, ev0, ev1))) return rc;
         uint32_t st = 0;
         if ((rc = read_status(d_status, &st, s))) return rc;
         if (st & STATUS_BADINPUT) return set_error(BN_EINVAL, "bn_build_scores: a data value is >= its arity");
@@ -700,6 +703,32 @@ extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t*
     guard.ok = true;
     *out = t;
     return BN_OK;
+}
+
+extern "C" int bn_build_scores(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                               const double* R, const bn_score_params* params, int mem,
+                               void* stream, bn_table** out)
+{
+    return build_scores_impl(data, m, n, arity, k, R, params, mem, stream, out, nullptr, nullptr);
+}
+
+extern "C" int bn_build_scores_profiled(const uint8_t* data, int m, int n, const uint8_t* arity, int k,
+                                        const double* R, const bn_score_params* params, int mem,
+                                        void* stream, bn_table** out, double* build_ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__);
+    }
+    int rc = build_scores_impl(data, m, n, arity, k, R, params, mem, stream, out, e0, e1);
+    float ms = 0.f;
+    if (rc == BN_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "cudaEventElapsedTime", __FILE__, __LINE__);
+    if (build_ms) *build_ms = (double)ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 extern "C" int bn_build_scores_batch(int count, const uint8_t* const* data, const int* m, const int* n,

@@ -136,3 +136,11 @@ def test_batch_build_equals_single_builds(gpu):
     with pytest.raises(gpu.BNError) as e:
         gpu.build_scores_batch(bad)
     assert e.value.code == gpu.EINVAL and "network 1" in str(e.value)
+
+
+def test_profiled_build_equals_build(gpu):
+    data, arity, k, R, _ = synth.workload("n20_k4_m1000")
+    t0 = gpu.build_scores(data, arity, k, R=R)
+    t1, ms = gpu.build_scores_profiled(data, arity, k, R=R)
+    assert ms > 0.0
+    assert np.array_equal(gpu.table_scores(t0), gpu.table_scores(t1))
