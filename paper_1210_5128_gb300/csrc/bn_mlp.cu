@@ -225,12 +225,13 @@ __global__ void k_bias(float* __restrict__ Z, const float* __restrict__ bias, in
     Z[idx] += bias[idx % N];
 }
 
-// output layer gradient of the BCE loss (one logit per row): block per row
+// output layer gradient of the BCE loss (one logit per row): block per row.  The row's
+// d loss / d logit and loss term go to grow[r] and lrow[r]; k_out_grad_w and k_loss_sum
+// sum them in row order, so the gradients and the loss do not depend on scheduling.
 __global__ void k_out_grad(const float* __restrict__ L, int ldl, const uint32_t* __restrict__ pairs,
-                           const float* __restrict__ alpha, int B, int Mp, int H, const bf16* __restrict__ H2,
-                           const float* __restrict__ Z2, const bf16* __restrict__ W3b, float* __restrict__ gW3,
-                           float* __restrict__ gb3, bf16* __restrict__ dZ2, bf16* __restrict__ dZ2T,
-                           float* __restrict__ loss)
+                           const float* __restrict__ alpha, int B, int Mp, int H, const float* __restrict__ Z2,
+                           const bf16* __restrict__ W3b, bf16* __restrict__ dZ2, bf16* __restrict__ dZ2T,
+                           float* __restrict__ grow, float* __restrict__ lrow)
 {
     const int r = blockIdx.x;
     float g = 0.f;
@@ -242,21 +243,59 @@ __global__ void k_out_grad(const float* __restrict__ L, int ldl, const uint32_t*
         const float a = alpha[r];
         g = (s - a) / (float)B;
         if (threadIdx.x == 0) {
-            const float ls = -(a * logf(s + 1e-30f) + (1.f - a) * logf(1.f - s + 1e-30f)) / (float)B;
-            atomicAdd(loss, ls);
-            atomicAdd(&gb3[p], g);
+            lrow[r] = -(a * logf(s + 1e-30f) + (1.f - a) * logf(1.f - s + 1e-30f)) / (float)B;
+            grow[r] = g;
         }
     }
     for (int c = threadIdx.x; c < H; c += blockDim.x) {
         bf16 dz = __float2bfloat16_rn(0.f);
         if (r < B) {
-            atomicAdd(&gW3[(size_t)p * H + c], g * __bfloat162float(H2[(size_t)r * H + c]));
             const float dh = g * __bfloat162float(W3b[(size_t)p * H + c]);
             dz = __float2bfloat16_rn(Z2[(size_t)r * H + c] > 0.f ? dh : 0.f);
         }
         dZ2[(size_t)r * H + c] = dz;
         dZ2T[(size_t)c * Mp + r] = dz;
     }
+}
+
+// gW3 and gb3 rows of the pairs the batch touches: the block of the first row holding a
+// pair sums that pair's rows in row order (the other rows of the pair leave it)
+__global__ void k_out_grad_w(const uint32_t* __restrict__ pairs, const float* __restrict__ grow, int B, int H,
+                             const bf16* __restrict__ H2, float* __restrict__ gW3, float* __restrict__ gb3)
+{
+    const int r = blockIdx.x;
+    const uint32_t p = pairs[r];
+    bool dup = false;
+    for (int q = threadIdx.x; q < r; q += blockDim.x) dup |= pairs[q] == p;
+    if (__syncthreads_or(dup)) return;                                  // block-uniform
+    for (int c = threadIdx.x; c < H; c += blockDim.x) {
+        float s = 0.f;
+        for (int q = r; q < B; ++q)
+            if (pairs[q] == p) s += grow[q] * __bfloat162float(H2[(size_t)q * H + c]);
+        gW3[(size_t)p * H + c] = s;
+    }
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int q = r; q < B; ++q)
+            if (pairs[q] == p) s += grow[q];
+        gb3[p] = s;
+    }
+}
+
+// the batch loss: the rows' terms in a fixed order (per thread a strided run, then a
+// fixed shared-memory tree)
+__global__ void k_loss_sum(const float* __restrict__ lrow, int B, float* __restrict__ loss)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int r = threadIdx.x; r < B; r += 256) s += lrow[r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0];
 }
 
 // dZ = bf16(dH * (Z > 0)), rows >= B -> 0, with the transposed copy
@@ -281,15 +320,23 @@ __global__ void k_colsum(const bf16* __restrict__ M, int N, int B, float* __rest
     out[c] = s;
 }
 
-// dE[order_r(p)][j] += dX[r][p*d + j]
-__global__ void k_embed_grad(const uint8_t* __restrict__ orders, const float* __restrict__ dX, int B, int n, int d,
+// inverse of each order: inv[r * 64 + v] = position of node v in order r
+__global__ void k_inv_orders(const uint8_t* __restrict__ orders, int n, uint8_t* __restrict__ inv)
+{
+    const int r = blockIdx.x, p = threadIdx.x;
+    if (p < n) inv[(size_t)r * 64 + orders[(size_t)r * n + p]] = (uint8_t)p;
+}
+
+// dE[v][j] = sum over the rows r, in row order, of dX[r][inv_r(v) d + j]
+__global__ void k_embed_grad(const uint8_t* __restrict__ inv, const float* __restrict__ dX, int B, int n, int d,
                              int ndp, float* __restrict__ gE)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * n * d) return;
-    const int r = (int)(idx / (n * d)), col = (int)(idx - (int64_t)r * n * d);
-    const int p = col / d, j = col - p * d;
-    atomicAdd(&gE[(size_t)orders[(size_t)r * n + p] * d + j], dX[(size_t)r * ndp + col]);
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * d) return;
+    const int v = idx / d, j = idx - v * d;
+    float s = 0.f;
+    for (int r = 0; r < B; ++r) s += dX[(size_t)r * ndp + (size_t)inv[(size_t)r * 64 + v] * d + j];
+    gE[idx] = s;
 }
 
 // Adam (Kingma & Ba): moments and the FP32 master weight
@@ -375,10 +422,13 @@ int bn::mlp_loss_grad_dev(bn_mlp* m, const uint8_t* d_orders, const uint32_t* d_
     BN_CUDA(cudaMemsetAsync(m->gE, 0, sizeof(float) * (size_t)m->n * m->d, s));
     BN_CUDA(cudaMemsetAsync(m->gW3, 0, sizeof(float) * (size_t)m->P * H, s));
     BN_CUDA(cudaMemsetAsync(m->gb3, 0, sizeof(float) * (size_t)m->P, s));
-    BN_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
-    k_out_grad<<<Mp, 256, 0, s>>>(m->L, m->Pp, d_pairs, d_alpha, B, Mp, H, m->H2, m->Z2, m->W3b, m->gW3, m->gb3,
-                                  m->dZ2, m->dZ2T, m->loss);
+    k_out_grad<<<Mp, 256, 0, s>>>(m->L, m->Pp, d_pairs, d_alpha, B, Mp, H, m->Z2, m->W3b, m->dZ2, m->dZ2T,
+                                  m->grow, m->lrow);
     BN_LAUNCH_CHECK("k_out_grad");
+    k_out_grad_w<<<B, 256, 0, s>>>(d_pairs, m->grow, B, H, m->H2, m->gW3, m->gb3);
+    BN_LAUNCH_CHECK("k_out_grad_w");
+    k_loss_sum<<<1, 256, 0, s>>>(m->lrow, B, m->loss);
+    BN_LAUNCH_CHECK("k_loss_sum");
     k_colsum<<<nblk(H), 256, 0, s>>>(m->dZ2, H, B, m->gb2);
     BN_LAUNCH_CHECK("k_colsum");
     // dW2 = dZ2^T H1 ; dH1 = dZ2 W2
@@ -391,7 +441,9 @@ int bn::mlp_loss_grad_dev(bn_mlp* m, const uint8_t* d_orders, const uint32_t* d_
     // dW1 = dZ1^T X ; dX = dZ1 W1
     if ((rc = gemm_tc(m->dZ1T, Mp, m->XT, Mp, m->gW1, m->ndp, H, m->ndp, Mp, m->status, s, m->ws, m->ws_elems))) return rc;
     if ((rc = gemm_tc(m->dZ1, H, m->W1T, H, m->dX, m->ndp, Mp, m->ndp, H, m->status, s, m->ws, m->ws_elems))) return rc;
-    k_embed_grad<<<nblk((int64_t)B * m->n * m->d), 256, 0, s>>>(d_orders, m->dX, B, m->n, m->d, m->ndp, m->gE);
+    k_inv_orders<<<B, 64, 0, s>>>(d_orders, m->n, m->inv);
+    BN_LAUNCH_CHECK("k_inv_orders");
+    k_embed_grad<<<nblk((int64_t)m->n * m->d), 256, 0, s>>>(m->inv, m->dX, B, m->n, m->d, m->ndp, m->gE);
     BN_LAUNCH_CHECK("k_embed_grad");
     return BN_OK;
 }
@@ -455,6 +507,7 @@ extern "C" int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, cons
         {&m->vE, nE}, {&m->vW1, nW1}, {&m->vb1, (size_t)H}, {&m->vW2, nW2}, {&m->vb2, (size_t)H},
         {&m->vW3, nW3}, {&m->vb3, (size_t)Pp}, {&m->Z1, (size_t)cap * H}, {&m->Z2, (size_t)cap * H},
         {&m->L, (size_t)cap * Pp}, {&m->dH1, (size_t)cap * H}, {&m->dX, (size_t)cap * ndp}, {&m->loss, 4},
+        {&m->grow, (size_t)cap}, {&m->lrow, (size_t)cap},
         {&m->ws, (size_t)8 * cap * std::max(std::max(Pp, ndp), H)}};
     std::vector<std::pair<bf16**, size_t>> b16 = {
         {&m->Eb, nE}, {&m->W1b, nW1}, {&m->W1T, nW1}, {&m->W2b, nW2}, {&m->W2T, nW2}, {&m->W3b, nW3},
@@ -468,6 +521,8 @@ extern "C" int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, cons
     off += 256;
     const size_t o_stage = off;                      // staging for host inputs: orders, pairs, alpha
     off += (size_t)round_up((int64_t)cap * n, 256) + (size_t)round_up((int64_t)cap * 4, 256) * 2;
+    const size_t o_inv = off;                        // inverse orders of a training batch
+    off += (size_t)round_up((int64_t)cap * 64, 256);
     cudaError_t e = cudaMalloc(&m->block, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -482,6 +537,7 @@ extern "C" int bn_mlp_create(int n, const bn_mlp_params* p, const float* E, cons
     m->stage_orders = base + o_stage;
     m->stage_pairs = (uint32_t*)(base + o_stage + (size_t)round_up((int64_t)cap * n, 256));
     m->stage_alpha = (float*)((uint8_t*)m->stage_pairs + (size_t)round_up((int64_t)cap * 4, 256));
+    m->inv = base + o_inv;
     m->bytes = off;
     m->ws_elems = (size_t)8 * cap * std::max(std::max(Pp, ndp), H);
     auto fail = [&](int rc) { bn_mlp_free(m); return rc; };

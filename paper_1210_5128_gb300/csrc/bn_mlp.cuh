@@ -21,6 +21,8 @@ struct bn_mlp {
     __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *dZ2, *dZ2T, *dZ1, *dZ1T;
     // FP32 activations
     float *Z1, *Z2, *L, *dH1, *dX, *loss;
+    float *grow, *lrow;            // per training row: d loss / d logit[pair] and loss term
+    uint8_t* inv = nullptr;        // [cap][64] inverse orders of a training batch
     float* ws = nullptr;           // split-K partials
     size_t ws_elems = 0;
     uint32_t* status;

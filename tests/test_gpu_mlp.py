@@ -139,3 +139,23 @@ def test_batch_above_capacity_rejected(gpu):
     with pytest.raises(gpu.BNError) as e:
         gpu.mlp_forward(net, synth.random_orders(6, 129, 1))
     assert e.value.code == gpu.EINVAL
+
+
+def test_training_steps_are_deterministic(gpu):
+    """Gradients are summed in a fixed order (no floating-point atomics): two networks
+    trained on the same batches hold the same bits, including batches that repeat a pair."""
+    n, d, H, B = 20, 16, 128, 200
+    w, _ = _weights(n, d, H, 4)
+    nets = [gpu.mlp_create(n, w, hidden=H, d=d, batch_cap=B, lr=2e-3) for _ in range(2)]
+    rng = np.random.default_rng(8)
+    for step in range(3):
+        orders = synth.random_orders(n, B, 30 + step)
+        pairs = rng.integers(0, 12, B).astype(np.uint32)          # few distinct pairs: many repeats
+        alpha = rng.uniform(0, 1, B).astype(np.float32)
+        losses = [gpu.mlp_loss_grad(net, orders, pairs, alpha) for net in nets]
+        assert losses[0] == losses[1]
+        for net in nets:
+            gpu.mlp_adam_step(net)
+    for name in ["E", "W1", "b1", "W2", "b2", "W3", "b3"]:
+        assert np.array_equal(gpu.mlp_read(nets[0], name), gpu.mlp_read(nets[1], name)), name
+        assert np.array_equal(gpu.mlp_read(nets[0], name, grad=True), gpu.mlp_read(nets[1], name, grad=True)), name
