@@ -744,12 +744,12 @@ def main():
                              "state only (the table stays in shared memory)"}
         avg_full = scan_ms_full / max(scan_l_full, 1)
         tests = items_prof * S / max(scan_l_full, 1)                 # (entry, item) tests per launch
-        roof_scan = {"kernel": "k_scan<1024,0> (full table, one launch per sampler step of all chains)",
+        roof_scan = {"kernel": "k_scan (full table, autotuned tiling, one launch per sampler step of all chains)",
                      "bound": "alu", "unit": "tests/s", "achieved": tests / (avg_full / 1000.0),
                      "peak": test_rate, "frac": tests / (avg_full / 1000.0) / test_rate,
                      "traffic": SCAN_TRAFFIC_BYTES,
-                     "peak_source": "measured in this run: bn_measure_test_rate (the scan's exact consistency "
-                                    "test on register operands, 8 x 256 threads per SM, CUDA events)",
+                     "peak_source": "measured in this run: bn_measure_test_rate (the scan's own inner loop over "
+                                    "1,024 entries resident in shared memory, 8 x 256 threads per SM, CUDA events)",
                      "per_launch": {"tests": tests, "avg_ms": avg_full, "launches": scan_l_full,
                                     "hbm_bytes_algorithmic": 4 * n * S + 8 * S,
                                     "hbm_frac_of_measured": (4 * n * S + 8 * S) / (avg_full / 1000.0) / 1e9 / hbm_peak},
