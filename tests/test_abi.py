@@ -91,3 +91,28 @@ def test_argument_checks_before_any_device_work(bn):
     assert L.bn_build_scores(data.ctypes.data, 4, 3, ar.ctypes.data, 1, None, None, 0, None, None) == bn.EINVAL
     assert L.bn_score_orders(None, None, 1, None, None, 0, None) == bn.EINVAL
     assert L.bn_table_info(None, None, None, None, None) == bn.EINVAL
+
+
+def test_argument_checks_of_batch_and_run_calls(bn):
+    """The calls added for batches, runs and measurement reject bad arguments before any
+    device work (the messages name the offending network)."""
+    L = bn.lib()
+    good = np.zeros((4, 3), np.uint8)
+    bad = np.full((4, 3), 7, np.uint8)
+    ar = np.full(3, 2, np.uint8)
+    datas = (C.c_void_p * 2)(good.ctypes.data, bad.ctypes.data)
+    ars = (C.c_void_p * 2)(ar.ctypes.data, ar.ctypes.data)
+    ms, ns, ks = (C.c_int * 2)(4, 4), (C.c_int * 2)(3, 3), (C.c_int * 2)(1, 1)
+    out = (C.c_void_p * 2)()
+    assert L.bn_build_scores_batch(2, datas, ms, ns, ars, ks, None, None, 0, None, out) == bn.EINVAL
+    assert "network 1" in bn.last_error() and out[0] is None and out[1] is None
+    assert L.bn_build_scores_batch(0, datas, ms, ns, ars, ks, None, None, 0, None, out) == bn.EINVAL
+    p = bn.MCMCParams(4, 0, 1, 0, 0, 0, 0, 0, 0, 0.1, 0, 0, None)
+    tabs = (C.c_void_p * 1)(None)
+    ps = (bn.MCMCParams * 1)(p)
+    assert L.bn_mcmc_run_batch(0, tabs, ps, 10, None, None, None, None, None, None) == bn.EINVAL
+    assert L.bn_mcmc_run_batch(1, tabs, ps, 10, None, None, None, None, None, None) == bn.EINVAL
+    assert "network 0" in bn.last_error()
+    assert L.bn_mcmc_run(None, C.byref(p), 10, None, None, None, None, None, None) == bn.EINVAL
+    assert L.bn_chains_set_learned_launch(None, 0) == bn.EINVAL
+    assert L.bn_measure_test_rate(None, None) == bn.EINVAL
