@@ -44,7 +44,8 @@ static constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 template <int SUB>
 struct ScanCfg {
     static constexpr int STAGES = SUB >= 2048 ? 3 : (SUB >= 1024 ? 4 : 8);
-    static constexpr size_t SMEM = (size_t)STAGES * SUB * (sizeof(uint32_t) + sizeof(uint64_t)) + 8 * STAGES;
+    // stages, then a full and an empty mbarrier per stage
+    static constexpr size_t SMEM = (size_t)STAGES * SUB * (sizeof(uint32_t) + sizeof(uint64_t)) + 16 * STAGES;
 };
 
 struct ScanArgs {
@@ -155,14 +156,15 @@ __device__ __forceinline__ uint64_t next_set(uint64_t m, int N, int k, int& size
 }
 
 template <int SCAN_SUB, bool UNRANK>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
+__global__ void __launch_bounds__(SCAN_THREADS, 4) k_scan(ScanArgs A)
 {
     constexpr int SCAN_STAGES = ScanCfg<SCAN_SUB>::STAGES;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* s_msk = (uint64_t*)smem;                                          // [STAGES][SUB]
     uint32_t* s_sp = (uint32_t*)(smem + sizeof(uint64_t) * SCAN_STAGES * SCAN_SUB);
     uint64_t* bar = (uint64_t*)(smem + (sizeof(uint64_t) + sizeof(uint32_t)) * SCAN_STAGES * SCAN_SUB);
-    uint64_t* s_bin = bar + SCAN_STAGES;                                        // C(c, t) (UNRANK)
+    uint64_t* ebar = bar + SCAN_STAGES;                                         // stage consumed by every warp
+    uint64_t* s_bin = ebar + SCAN_STAGES;                                       // C(c, t) (UNRANK)
 
     const int node = blockIdx.x / A.nchunk;
     const int chunk = blockIdx.x - node * A.nchunk;
@@ -194,7 +196,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     if (threadIdx.x == 0) {
         pol_stream = l2_policy_evict_first();
         pol_keep = l2_policy_evict_last();
-        for (int s = 0; s < SCAN_STAGES; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < SCAN_STAGES; ++s) {
+            mbar_init(&bar[s], 1);
+            mbar_init(&ebar[s], SCAN_WARPS);
+        }
         fence_mbar_init();
     }
     if (UNRANK)
@@ -208,59 +213,117 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs A)
     }
 
     uint32_t b0 = SPOS_NONE, b1 = SPOS_NONE;
-    int it = 0;
-    bool timed_out = false;
-    for (; it < nsub; ++it) {
-        const int st = it % SCAN_STAGES;
-        const uint32_t parity = (uint32_t)((it / SCAN_STAGES) & 1);
-        if (UNRANK) {
-            // this stage's masks: every thread a run of SUB / 256 consecutive ranks
-            constexpr int PER = SCAN_SUB / SCAN_THREADS;
-            const int64_t base = e0 + (int64_t)it * SCAN_SUB;
-            const int64_t r0 = base + (int64_t)threadIdx.x * PER;
-            uint64_t* dst = s_msk + st * SCAN_SUB + threadIdx.x * PER;
-            if (r0 < e1) {
-                int size = 0;
-                uint64_t m = r0 < A.S ? unrank_set((uint64_t)r0, A.N, A.k, s_bin, size) : ~0ull;
-                if (r0 >= A.S) size = A.k + 1;
-                dst[0] = m;
-#pragma unroll
-                for (int q = 1; q < PER; ++q) {
-                    m = next_set(m, A.N, A.k, size);
-                    dst[q] = m;
+    if constexpr (!UNRANK) {
+        // Warps run decoupled: each waits for a stage to land (full barrier), tests it,
+        // and releases it (empty barrier, one arrival per warp); thread 0 re-fills a stage
+        // once every warp has released it, SCAN_STAGES stages ahead of its own position.
+        // A wait that runs out sets s_abort, and every warp leaves at its next stage.
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = 0;
+        __syncthreads();
+        int issued = min(nsub, SCAN_STAGES);
+        for (int it = 0; it < nsub; ++it) {
+            const int st = it % SCAN_STAGES;
+            const uint32_t parity = (uint32_t)((it / SCAN_STAGES) & 1);
+            // warp-uniform decisions: lane 0's view of the abort flag, all lanes' waits
+            if (__shfl_sync(0xffffffffu, *(volatile int*)&s_abort, 0)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], parity, WAIT_TIMEOUT_NS))) {
+                if (lane == 0) {
+                    *(volatile int*)&s_abort = 1;
+                    atomicOr(A.status, STATUS_TIMEOUT);
+                }
+                break;
+            }
+            if (warp_on) {
+                const int64_t base = e0 + (int64_t)it * SCAN_SUB;
+                const int pairs = (int)min((int64_t)SCAN_SUB, e1 - base) >> 1;
+                const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
+                const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
+#pragma unroll 32
+                for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
+                    const uint2 pp = P[j];
+                    const uint4 mm = ((const uint4*)M)[j];
+                    test_min(b0, mm.x, mm.y, nlo, nhi, pp.x);
+                    test_min(b1, mm.z, mm.w, nlo, nhi, pp.y);
                 }
             }
-            __syncthreads();
-        }
-        const bool ok = mbar_wait_bounded(&bar[st], parity, WAIT_TIMEOUT_NS);
-        if (ok && warp_on) {
-            const int64_t base = e0 + (int64_t)it * SCAN_SUB;
-            const int pairs = (int)min((int64_t)SCAN_SUB, e1 - base) >> 1;
-            const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
-            const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
-#pragma unroll 32
-            for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
-                const uint2 pp = P[j];
-                const uint4 mm = ((const uint4*)M)[j];
-                test_min(b0, mm.x, mm.y, nlo, nhi, pp.x);
-                test_min(b1, mm.z, mm.w, nlo, nhi, pp.y);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ebar[st]);
+            if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
+                // (on a timeout no break here: warp 0 leaves together at the next check)
+                if (!mbar_wait_bounded(&ebar[st], parity, WAIT_TIMEOUT_NS)) {
+                    *(volatile int*)&s_abort = 1;
+                    atomicOr(A.status, STATUS_TIMEOUT);
+                } else {
+                    const int64_t nb = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
+                    scan_issue<SCAN_SUB, UNRANK>(A, node, nb, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB,
+                                                 &bar[st], pol_stream, pol_keep);
+                    issued = it + SCAN_STAGES + 1;
+                }
             }
         }
-        if (__syncthreads_or(!ok)) { timed_out = true; break; }
-        if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
-            const int64_t base = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
-            scan_issue<SCAN_SUB, UNRANK>(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st],
-                                         pol_stream, pol_keep);
-        }
-    }
-    if (timed_out) {
         if (threadIdx.x == 0) {
-            atomicOr(A.status, STATUS_TIMEOUT);
-            // let copies already in flight land before the CTA's shared memory goes away
-            for (int j = it; j < nsub && j < it + SCAN_STAGES; ++j)
+            // no copy may still be in flight when the block's shared memory goes away
+            for (int j = max(0, issued - SCAN_STAGES); j < issued; ++j)
                 mbar_wait_bounded(&bar[j % SCAN_STAGES], (uint32_t)((j / SCAN_STAGES) & 1), WAIT_TIMEOUT_NS);
         }
-        return;
+        __syncthreads();
+        if (s_abort) return;                                        // block-uniform after the barrier
+    } else {
+        int it = 0;
+        bool timed_out = false;
+        for (; it < nsub; ++it) {
+            const int st = it % SCAN_STAGES;
+            const uint32_t parity = (uint32_t)((it / SCAN_STAGES) & 1);
+            if (UNRANK) {
+                // this stage's masks: every thread a run of SUB / 256 consecutive ranks
+                constexpr int PER = SCAN_SUB / SCAN_THREADS;
+                const int64_t base = e0 + (int64_t)it * SCAN_SUB;
+                const int64_t r0 = base + (int64_t)threadIdx.x * PER;
+                uint64_t* dst = s_msk + st * SCAN_SUB + threadIdx.x * PER;
+                if (r0 < e1) {
+                    int size = 0;
+                    uint64_t m = r0 < A.S ? unrank_set((uint64_t)r0, A.N, A.k, s_bin, size) : ~0ull;
+                    if (r0 >= A.S) size = A.k + 1;
+                    dst[0] = m;
+    #pragma unroll
+                    for (int q = 1; q < PER; ++q) {
+                        m = next_set(m, A.N, A.k, size);
+                        dst[q] = m;
+                    }
+                }
+                __syncthreads();
+            }
+            const bool ok = mbar_wait_bounded(&bar[st], parity, WAIT_TIMEOUT_NS);
+            if (ok && warp_on) {
+                const int64_t base = e0 + (int64_t)it * SCAN_SUB;
+                const int pairs = (int)min((int64_t)SCAN_SUB, e1 - base) >> 1;
+                const uint2* P = (const uint2*)(s_sp + st * SCAN_SUB);
+                const ulonglong2* M = (const ulonglong2*)(s_msk + st * SCAN_SUB);
+    #pragma unroll 32
+                for (int j = sp * LPI + sub; j < pairs; j += split * LPI) {
+                    const uint2 pp = P[j];
+                    const uint4 mm = ((const uint4*)M)[j];
+                    test_min(b0, mm.x, mm.y, nlo, nhi, pp.x);
+                    test_min(b1, mm.z, mm.w, nlo, nhi, pp.y);
+                }
+            }
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            if (threadIdx.x == 0 && it + SCAN_STAGES < nsub) {
+                const int64_t base = e0 + (int64_t)(it + SCAN_STAGES) * SCAN_SUB;
+                scan_issue<SCAN_SUB, UNRANK>(A, node, base, e1, s_sp + st * SCAN_SUB, s_msk + st * SCAN_SUB, &bar[st],
+                                             pol_stream, pol_keep);
+            }
+        }
+        if (timed_out) {
+            if (threadIdx.x == 0) {
+                atomicOr(A.status, STATUS_TIMEOUT);
+                // let copies already in flight land before the CTA's shared memory goes away
+                for (int j = it; j < nsub && j < it + SCAN_STAGES; ++j)
+                    mbar_wait_bounded(&bar[j % SCAN_STAGES], (uint32_t)((j / SCAN_STAGES) & 1), WAIT_TIMEOUT_NS);
+            }
+            return;
+        }
     }
     uint32_t b = min(b0, b1);
     for (int off = 1; off < LPI; off <<= 1) b = min(b, __shfl_xor_sync(0xffffffffu, b, off));
