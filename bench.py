@@ -178,7 +178,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(args.chains),
+        "data": "synthetic", "config": run_config(args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
                          "sample": f"{args.steps * nt} order evaluations ({tot:.1f} s) by the oracle at n=60, "
                                    f"k=4, {nt} per step (one per host thread), on a seeded stand-in table of "
@@ -187,6 +187,12 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_config(args):
+    """The config both arms print (the same workload and unit of work)."""
+    return dict(config_dict(args.chains), iters_per_step=args.iters_per_step,
+                step=f"{args.iters_per_step} MH iterations of every chain")
 
 
 def config_dict(chains, scan="pruned"):
@@ -773,8 +779,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(args.chains), iters_per_step=args.iters_per_step,
-                           step=f"{args.iters_per_step} MH iterations of every chain"),
+            "config": run_config(args),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "note": f"per call: bn_build_scores from host data + pruning + bn_mcmc_run of {e2e_steps} "
                             f"steps x {args.chains} chains + results to host"},

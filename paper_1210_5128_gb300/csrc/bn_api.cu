@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "bn_internal.cuh"
 
 namespace bn {
@@ -36,6 +38,43 @@ int device_id()
     int d = 0;
     cudaGetDevice(&d);
     return d;
+}
+
+unsigned long long context_id()
+{
+    typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+    typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+bool first_in_context(unsigned long long* slots)
+{
+    static std::mutex mu;
+    const int d = device_id();
+    if (d < 0 || d >= 64) return true;
+    const unsigned long long id = context_id();
+    std::lock_guard<std::mutex> g(mu);
+    if (id != 0 && slots[d] == id) return false;
+    slots[d] = id;
+    return true;
 }
 
 int sm_count()

@@ -21,6 +21,12 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 void count_launches(int64_t k);
 int sm_count();                      // SMs of the current device
 int device_id();
+// Identity of the calling thread's current CUDA context (0 when the driver cannot say).
+unsigned long long context_id();
+// True the first time it is called in the current context of the current device with
+// this call site's `slots` (64 zero-initialised entries): per-context set-up, such as a
+// kernel's shared-memory attribute, which a context destroyed and created again loses.
+bool first_in_context(unsigned long long* slots);
 
 #define BN_CUDA(call)                                                                  \
     do {                                                                               \

@@ -1201,13 +1201,11 @@ static int learned_weights(bn_chains* ch, cudaStream_t s)
     lp->g3.mode = 1;
     lp->g3.logits = (float*)lp->L.logits;
     lp->g3.part = (float2*)lp->L.part;
-    static bool attr[64] = {false};
-    const int dv = device_id();
-    if (dv < 64 && !attr[dv]) {
+    static unsigned long long ctx[64] = {0};
+    if (first_in_context(ctx)) {
         BN_CUDA(cudaFuncSetAttribute(k_learned_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)lgemm_smem(LR_MAX_H)));
         BN_CUDA(cudaFuncSetAttribute(k_learned_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, LR_STAGE_MAX));
-        attr[dv] = true;
     }
     if (lp->exec) {
         cudaGraphExecDestroy(lp->exec);

@@ -929,13 +929,11 @@ int build_survivor_cache(bn_table* t, cudaStream_t s)
 
 static int fused_smem_setup(int cap, size_t* smem)
 {
-    static bool done[64] = {false};
-    const int d = device_id();
+    static unsigned long long ctx[64] = {0};
     const size_t mx = surv_cache_stride(SURV_CAP_MAX);
-    if (d < 64 && !done[d]) {
+    if (first_in_context(ctx)) {
         BN_CUDA(cudaFuncSetAttribute(k_chain_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-        done[d] = true;
     }
     *smem = surv_cache_stride(cap);
     return BN_OK;

@@ -156,12 +156,9 @@ int gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, i
 {
     if (M % TC_BM || N % TC_BN || K % TC_BK)
         return set_error(BN_EINVAL, "gemm: M=%d N=%d K=%d must be multiples of 128, 128, 64", M, N, K);
-    static bool attr[64] = {false};
-    const int d = device_id();
-    if (d < 64 && !attr[d]) {
+    static unsigned long long ctx[64] = {0};
+    if (first_in_context(ctx))
         BN_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        attr[d] = true;
-    }
     const int tiles = (M / TC_BM) * (N / TC_BN);
     int split = 1;
     if (ws) {

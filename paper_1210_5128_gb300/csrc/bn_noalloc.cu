@@ -11,7 +11,6 @@
 #include <algorithm>
 #include <mutex>
 
-#include <cuda.h>
 
 #include "bn_table.cuh"
 
@@ -27,9 +26,6 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES
 // context it belongs to: a context destroyed and created again (cudaDeviceReset, or the
 // primary context released and retained anew) has a new identity, and the address is
 // looked up again.  Without the driver's context identity the lookup runs on every call.
-typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
-typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
-
 struct NoallocSlot {
     unsigned long long ctx = 0;
     void* ptr = nullptr;
@@ -37,34 +33,12 @@ struct NoallocSlot {
 static std::mutex g_noalloc_mu;
 static NoallocSlot g_noalloc_slot[64];
 
-// identity of the calling thread's current context (false: not available)
-static bool current_context_id(unsigned long long* id)
-{
-    static CtxGetCurrentFn get_current = nullptr;
-    static CtxGetIdFn get_id = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_current = (CtxGetCurrentFn)f;
-        f = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_id = (CtxGetIdFn)f;
-        cudaGetLastError();
-    });
-    CUcontext c = nullptr;
-    return get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, id) == CUDA_SUCCESS;
-}
-
 static int noalloc_scratch(void** out)
 {
     const int d = device_id();
     if (d < 0 || d >= 64) return set_error(BN_EUNSUPPORTED, "bn_score_orders_noalloc: device id %d", d);
-    unsigned long long ctx = 0;
-    const bool known = current_context_id(&ctx);
+    const unsigned long long ctx = context_id();
+    const bool known = ctx != 0;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     NoallocSlot& slot = g_noalloc_slot[d];
     if (!known || !slot.ptr || slot.ctx != ctx) {

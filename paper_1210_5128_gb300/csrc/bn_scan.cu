@@ -335,13 +335,10 @@ static constexpr size_t SCAN_BIN_BYTES = 8 * 65 * (MAXK + 1);   // binomial tabl
 template <int SUB, bool UNRANK>
 static int scan_variant(const ScanArgs& A, dim3 grid, cudaStream_t s)
 {
-    static bool attr_set[64] = {false};
+    static unsigned long long ctx[64] = {0};
     const size_t smem = ScanCfg<SUB>::SMEM + (UNRANK ? SCAN_BIN_BYTES : 0);
-    const int d = device_id();
-    if (d < 64 && !attr_set[d]) {
+    if (first_in_context(ctx))
         BN_CUDA(cudaFuncSetAttribute(k_scan<SUB, UNRANK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[d] = true;
-    }
     k_scan<SUB, UNRANK><<<grid, SCAN_THREADS, smem, s>>>(A);
     BN_LAUNCH_CHECK("k_scan");
     return BN_OK;
@@ -476,14 +473,12 @@ int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_
                       cudaStream_t s)
 {
     const size_t smem = ns_smem(t->n);
-    static bool attr[64] = {false};
-    const int d = device_id();
-    if (d < 64 && !attr[d]) {
+    static unsigned long long ctx[64] = {0};
+    if (first_in_context(ctx)) {
         BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
         BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
         BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
         BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
-        attr[d] = true;
     }
     // threads per (order, node) pair: as many as the block holds, at most eight
     int T = 1;
@@ -646,16 +641,15 @@ using namespace bn;
 // would unmap it at every synchronisation and map it again on the next call)
 static void keep_pool_mapped()
 {
-    static bool done[64] = {false};
+    static unsigned long long ctx[64] = {0};
+    if (!first_in_context(ctx)) return;
     const int d = device_id();
-    if (d < 0 || d >= 64 || done[d]) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
         uint64_t thr = (uint64_t)256 << 20;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     cudaGetLastError();
-    done[d] = true;
 }
 
 static int score_orders_impl(const bn_table* t, const uint8_t* orders, int B, uint32_t* best_rank,
