@@ -648,7 +648,7 @@ def main():
                                 lr=2e-3)
             learned, f_learned = _ess_run(bn, torch, table, args.chains, seed + 2, pre, args.ess_steps, stream,
                                           net=net, train_steps=args.train_steps, thin=args.ess_thin)
-            # long plain run (8x) as the judge of the learned sampler's edge frequencies
+            # long plain run (8x) as the reference for the learned sampler's edge frequencies
             long_ch = bn.chains_create(table, args.chains, seed + 3, burn_in=pre)
             bn.chains_step(long_ch, pre + 8 * args.ess_steps, stream=stream.cuda_stream)
             f_long = bn.chains_read(long_ch, "edge_counts").sum(0) / (args.chains * 8 * args.ess_steps)

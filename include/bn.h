@@ -44,7 +44,7 @@ extern "C" {
 #define BN_ENOMEM       -2   /* a device or host allocation failed */
 #define BN_ECUDA        -3   /* a CUDA runtime call failed (message has the CUDA error) */
 #define BN_ETIMEOUT     -4   /* a bounded device-side wait expired; the kernel gave up */
-#define BN_EUNSUPPORTED -5   /* valid request outside this build's limits */
+#define BN_EUNSUPPORTED -5   /* valid request outside the library's limits */
 
 #define BN_MEM_HOST   0
 #define BN_MEM_DEVICE 1
