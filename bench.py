@@ -207,7 +207,7 @@ def config_dict(chains, scan="pruned"):
 
 
 L2_FLUSH_BYTES = 512 << 20 # written, then another buffer read, between timed steps (L2 is 129 MB)
-SCORE_B = (1, 2, 4, 8, 16, 64, 256, 1024)   # orders per bn_score_orders call in the scoring sweep
+SCORE_B = (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024)   # orders per bn_score_orders call in the scoring sweep
 ISSUE_PER_SM = 4           # warp schedulers per SM, one warp instruction per clock each
 # ncu smsp__inst_executed.sum of k_chain_fused<1> at this workload (256 chains, 1,000-step
 # launches), per chain per MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum
@@ -535,7 +535,7 @@ def main():
             times.append(1000.0 * bn.score_orders_profiled(table, orders)[2])
         us = float(np.median(times))
         tests = float(n) * S * B                 # (entry, order) consistency tests of one pass
-        hbm_leg.append({"orders": B, "kernel": "k_scan_nodes" if n * B <= 256 else "k_scan",
+        hbm_leg.append({"orders": B, "kernel": "k_scan_nodes" if n * ((B + 7) // 8) <= 1024 else "k_scan",
                         "scan_us": us, "scan_us_mean": float(np.mean(times)), "calls": len(times),
                         "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
                         "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak,

@@ -18,6 +18,7 @@
 // memory speed instead of one active lane per warp).  Chunks combine with atomicMin.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "bn_table.cuh"
 
@@ -370,21 +371,25 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
 }
 
 // ---------------------------------------------------------------------------------
-// A few orders for every node (n x B <= 256 items, bn_score_orders): a block owns a slice
-// of the rank range for all nodes and orders, so the shared candidate-mask table is read
-// once per slice instead of once per node, and the slice's sorted positions of all nodes
-// come from the entry-major copy spos_t as one contiguous bulk copy per stage.  Thread
-// (b, i) tests every entry of the slice for node i of order b; the threads of a warp read
-// consecutive words of a staged row.
+// Up to 1,024 (node, order group) items (bn_score_orders; order groups of up to eight
+// orders): a block owns a slice of the rank range for all nodes and orders, so the
+// shared candidate-mask table is read once per slice instead of once per node, and the
+// slice's sorted positions of all nodes come from the entry-major copy spos_t as one
+// contiguous bulk copy per stage.  spos_t keeps the two positions of ranks 2j and 2j + 1
+// of node i side by side ([Sp / 2][n][2]), so a thread takes an entry pair's two masks by
+// one 16-byte and its node's two positions by one 8-byte shared-memory load, and tests
+// them against the R orders of its group held in registers.
 // ---------------------------------------------------------------------------------
 static constexpr int NS_SUB = 128;             // entries per stage
 static constexpr int NS_STAGES = 3;
+static constexpr int NS_RMAX = 8;              // orders per thread
+static constexpr int NS_MAX_ITEMS = 1024;      // (node, order group) items: one thread each
 
 __host__ __device__ constexpr size_t ns_stage_bytes(int n) { return (size_t)NS_SUB * 8 + (size_t)n * NS_SUB * 4; }
 __host__ __device__ constexpr size_t ns_smem(int n) { return NS_STAGES * ns_stage_bytes(n) + 8 * NS_STAGES; }
 
 struct NodeScanArgs {
-    const uint32_t* spos_t;        // [Sp][n]
+    const uint32_t* spos_t;        // [Sp / 2][n][2]
     const uint64_t* pst;
     int64_t Sp;
     int n, B;
@@ -394,10 +399,11 @@ struct NodeScanArgs {
     uint32_t* status;
 };
 
-// T consecutive threads per (order, node) pair; thread `sub` tests the entry pairs
-// (2j, 2j + 1), j = sub mod T, of every staged slice
-template <int T>
-__global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
+// Item g = i * BG + c (node i, order group c: orders c * R .. c * R + R - 1, those below
+// B) takes T consecutive threads; thread `sub` of an item tests the entry pairs
+// (2j, 2j + 1), j = sub mod T, of every staged slice against the group's orders.
+template <int T, int R>
+__global__ void __launch_bounds__(T == 1 ? 1024 : 256) k_scan_nodes(NodeScanArgs A)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const size_t SB = ns_stage_bytes(A.n);
@@ -407,11 +413,22 @@ __global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
     if (e0 >= e1) return;                                           // block-uniform
     const int nsub = (int)((e1 - e0) / NS_SUB);
     const int tid = threadIdx.x;
-    const int pairs = A.n * A.B;
-    const bool active = tid < pairs * T;
-    const int pr = tid / T, sub = tid - pr * T;
-    const int b = active ? pr / A.n : 0, i = active ? pr - b * A.n : 0;
-    const uint64_t npc = active ? ~A.list_pc[(size_t)i * A.B + b] : ~0ull;
+    const int BG = (A.B + R - 1) / R;
+    const int g = tid / T, sub = tid - g * T;
+    const bool active = g < A.n * BG;
+    const int i = active ? g / BG : 0, c = active ? g - i * BG : 0;
+    // predecessor masks of the group's orders, complemented (an unused slot tests only
+    // the empty set and is never written back)
+    uint32_t nlo[R], nhi[R], best0[R], best1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int b = c * R + r;
+        const uint64_t pc = (active && b < A.B) ? A.list_pc[(size_t)i * A.B + b] : 0ull;
+        nlo[r] = ~(uint32_t)pc;
+        nhi[r] = ~(uint32_t)(pc >> 32);
+        best0[r] = SPOS_NONE;
+        best1[r] = SPOS_NONE;
+    }
     const uint32_t rows = (uint32_t)(A.n * NS_SUB * 4);
     uint64_t pol_stream = 0, pol_keep = 0;
     if (tid == 0) {
@@ -431,7 +448,6 @@ __global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
     };
     if (tid == 0)
         for (int st = 0; st < NS_STAGES && st < nsub; ++st) issue(st, st);
-    uint32_t best0 = SPOS_NONE, best1 = SPOS_NONE;
     const int n = A.n;
     int it = 0;
     bool timed_out = false;
@@ -439,15 +455,18 @@ __global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
         const int st = it % NS_STAGES;
         const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS_STAGES) & 1), WAIT_TIMEOUT_NS);
         if (ok && active) {
-            const ulonglong2* M2 = (const ulonglong2*)(smem + (size_t)st * SB);
-            const uint32_t* P = (const uint32_t*)(smem + (size_t)st * SB + NS_SUB * 8) + i;
-#pragma unroll
+            const uint4* M2 = (const uint4*)(smem + (size_t)st * SB);
+            const uint2* P2 = (const uint2*)(smem + (size_t)st * SB + NS_SUB * 8) + i;
+#pragma unroll(R >= 4 ? 4 : 8)
             for (int q = 0; q < NS_SUB / 2 / T; ++q) {
                 const int j = q * T + sub;
-                const ulonglong2 mm = M2[j];
-                const uint32_t p0 = P[(2 * j) * n], p1 = P[(2 * j + 1) * n];
-                if ((mm.x & npc) == 0ull) best0 = min(best0, p0);
-                if ((mm.y & npc) == 0ull) best1 = min(best1, p1);
+                const uint4 mm = M2[j];
+                const uint2 pp = P2[j * n];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    test_min(best0[r], mm.x, mm.y, nlo[r], nhi[r], pp.x);
+                    test_min(best1[r], mm.z, mm.w, nlo[r], nhi[r], pp.y);
+                }
             }
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
@@ -461,38 +480,87 @@ __global__ void __launch_bounds__(256) k_scan_nodes(NodeScanArgs A)
         }
         return;
     }
-    uint32_t best = min(best0, best1);
 #pragma unroll
-    for (int off = 1; off < T; off <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-    if (active && sub == 0 && best != SPOS_NONE) atomicMin(&A.list_best[(size_t)i * A.B + b], best);
+    for (int r = 0; r < R; ++r) {
+        uint32_t best = min(best0[r], best1[r]);
+#pragma unroll
+        for (int off = 1; off < T; off <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+        const int b = c * R + r;
+        if (active && sub == 0 && b < A.B && best != SPOS_NONE) atomicMin(&A.list_best[(size_t)i * A.B + b], best);
+    }
 }
 
-bool scan_nodes_fits(const bn_table* t, int B) { return t->scan_mode == BN_SCAN_FULL && B >= 1 && t->n * B <= 256; }
+// launch shape of k_scan_nodes for n nodes and B orders: R orders per thread (as few
+// groups as eight orders a thread allow, the orders spread evenly over them), T threads an
+// item while 256 threads hold them, else one thread an item in blocks of up to 1,024
+struct NsShape {
+    int T, R, threads;
+};
+
+static NsShape ns_shape(int n, int B)
+{
+    const int BG = (B + NS_RMAX - 1) / NS_RMAX;
+    const int R = (B + BG - 1) / BG;
+    const int items = n * BG;
+    int T = 1;
+    while (T < 8 && 2 * T * items <= 256) T *= 2;
+    return {T, R, items * T <= 256 ? 256 : (int)round_up(items, 32)};
+}
+
+bool scan_nodes_fits(const bn_table* t, int B)
+{
+    return t->scan_mode == BN_SCAN_FULL && B >= 1 && (int64_t)t->n * ((B + NS_RMAX - 1) / NS_RMAX) <= NS_MAX_ITEMS;
+}
+
+template <int T, int R>
+static void ns_launch(unsigned grid, int threads, size_t smem, cudaStream_t s, const NodeScanArgs& A)
+{
+    k_scan_nodes<T, R><<<grid, threads, smem, s>>>(A);
+}
+
+typedef void (*NsLaunchFn)(unsigned, int, size_t, cudaStream_t, const NodeScanArgs&);
+typedef void (*NsKernelFn)(NodeScanArgs);
+
+template <int T>
+static void ns_table_row(NsLaunchFn* l, NsKernelFn* k)
+{
+    l[0] = ns_launch<T, 1>; l[1] = ns_launch<T, 2>; l[2] = ns_launch<T, 3>; l[3] = ns_launch<T, 4>;
+    l[4] = ns_launch<T, 5>; l[5] = ns_launch<T, 6>; l[6] = ns_launch<T, 7>; l[7] = ns_launch<T, 8>;
+    k[0] = k_scan_nodes<T, 1>; k[1] = k_scan_nodes<T, 2>; k[2] = k_scan_nodes<T, 3>; k[3] = k_scan_nodes<T, 4>;
+    k[4] = k_scan_nodes<T, 5>; k[5] = k_scan_nodes<T, 6>; k[6] = k_scan_nodes<T, 7>; k[7] = k_scan_nodes<T, 8>;
+}
 
 int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_t* list_best, uint32_t* status,
                       cudaStream_t s)
 {
+    static_assert(NS_RMAX == 8, "one table row per T holds R = 1..8");
+    static NsLaunchFn launch[4][NS_RMAX];
+    static NsKernelFn kern[4][NS_RMAX];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        ns_table_row<1>(launch[0], kern[0]);
+        ns_table_row<2>(launch[1], kern[1]);
+        ns_table_row<4>(launch[2], kern[2]);
+        ns_table_row<8>(launch[3], kern[3]);
+    });
     const size_t smem = ns_smem(t->n);
     static unsigned long long ctx[64] = {0};
-    if (first_in_context(ctx)) {
-        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
-        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
-        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
-        BN_CUDA(cudaFuncSetAttribute(k_scan_nodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem(MAXN)));
-    }
-    // threads per (order, node) pair: as many as the block holds, at most eight
-    int T = 1;
-    while (T < 8 && 2 * T * t->n * B <= 256) T *= 2;
-    // whole waves: as many blocks per SM as shared memory holds (at most four)
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(220 * 1024) / smem));
+    if (first_in_context(ctx))
+        for (int a = 0; a < 4; ++a)
+            for (int r = 0; r < NS_RMAX; ++r)
+                BN_CUDA(cudaFuncSetAttribute(kern[a][r], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ns_smem(MAXN)));
+    const NsShape sh = ns_shape(t->n, B);
+    // whole waves: as many blocks per SM as its 2,048 threads and shared memory hold (at
+    // most four)
+    const int per_sm = (int)std::max<size_t>(
+        1, std::min<size_t>({(size_t)4, (size_t)(2048 / sh.threads), (size_t)(220 * 1024) / smem}));
     const int64_t want = (int64_t)sm_count() * per_sm;
     const int64_t chunk = round_up((t->Sp + want - 1) / want, NS_SUB);
     NodeScanArgs A{t->spos_t, t->pst, t->Sp, t->n, B, chunk, list_pc, list_best, status};
     const unsigned grid = (unsigned)((t->Sp + chunk - 1) / chunk);
-    if (T == 8) k_scan_nodes<8><<<grid, 256, smem, s>>>(A);
-    else if (T == 4) k_scan_nodes<4><<<grid, 256, smem, s>>>(A);
-    else if (T == 2) k_scan_nodes<2><<<grid, 256, smem, s>>>(A);
-    else k_scan_nodes<1><<<grid, 256, smem, s>>>(A);
+    const int a = sh.T == 8 ? 3 : (sh.T == 4 ? 2 : (sh.T == 2 ? 1 : 0));
+    launch[a][sh.R - 1](grid, sh.threads, smem, s, A);
     BN_LAUNCH_CHECK("k_scan_nodes");
     return BN_OK;
 }

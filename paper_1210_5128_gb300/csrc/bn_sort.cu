@@ -160,10 +160,12 @@ __global__ void k_rs_finish(const uint32_t* __restrict__ vals, int64_t N, int64_
     spos[(node0 + i) * Sp + r] = (uint32_t)p;
 }
 
-// spos_t[r][i] = spos[i][r]: 32 x 32 tiles through shared memory (coalesced both ways)
+// spos_t[r / 2][i][r % 2] = spos[i][r]: 32 x 32 tiles through shared memory, a thread
+// storing the two positions of a rank pair of one node as one 8-byte word (coalesced both
+// ways)
 __global__ void k_spos_transpose(const uint32_t* __restrict__ spos, int n, int64_t Sp, uint32_t* __restrict__ spos_t)
 {
-    __shared__ uint32_t tile[32][33];
+    __shared__ uint32_t tile[32][33];                      // [node][rank]
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int i0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;          // 32 x 8 threads
@@ -172,9 +174,10 @@ __global__ void k_spos_transpose(const uint32_t* __restrict__ spos, int n, int64
         if (i < n) tile[y][tx] = spos[(size_t)i * Sp + r0 + tx];
     }
     __syncthreads();
-    for (int y = ty; y < 32; y += 8) {
+    uint2* out = (uint2*)spos_t;
+    for (int y2 = ty; y2 < 16; y2 += 8) {
         const int i = i0 + tx;
-        if (i < n) spos_t[(size_t)(r0 + y) * n + i] = tile[tx][y];
+        if (i < n) out[(size_t)(r0 / 2 + y2) * n + i] = make_uint2(tile[tx][2 * y2], tile[tx][2 * y2 + 1]);
     }
 }
 

@@ -13,7 +13,7 @@ struct bn_table {
     uint32_t* spos = nullptr;  // [n][Sp] position of the entry when the node's entries are
                                // ordered by score descending, rank ascending (padding: ~0)
     uint32_t* srank = nullptr; // [n][Sp] inverse of spos: rank at sorted position p
-    uint32_t* spos_t = nullptr;// [Sp][n] spos entry-major (scans of a few orders for every node)
+    uint32_t* spos_t = nullptr;// [Sp / 2][n][2] spos entry-major, rank pairs side by side (k_scan_nodes)
     size_t bytes = 0;
     int scan_mode = 0;         // BN_SCAN_FULL, BN_SCAN_PRUNED or BN_SCAN_UNRANK
     // entries not dominated by a proper subset, per node in sorted-position order
@@ -71,8 +71,9 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
                 const uint64_t* list_pc, uint32_t* list_best, int cap, uint32_t* status,
                 cudaStream_t s);
 
-// The same for B orders of every node when n * B <= 256 and the table is scanned in full
-// (scan_nodes_fits): one pass over the rank range for all nodes (list layout [n][B]).
+// The same for B orders of every node when n * ceil(B / 8) <= 1,024 and the table is
+// scanned in full (scan_nodes_fits): one pass over the rank range for all nodes and
+// orders, up to eight orders a thread (list layout [n][B]).
 bool scan_nodes_fits(const bn_table* t, int B);
 int launch_scan_nodes(const bn_table* t, int B, const uint64_t* list_pc, uint32_t* list_best, uint32_t* status,
                       cudaStream_t s);

@@ -136,12 +136,14 @@ def test_n60_headline_launches_equal_full_table_and_oracle(gpu, oracle_n60):
     assert (E.sum((1, 2)) <= 2000 * n * k).all() and (np.diagonal(E, axis1=1, axis2=2) == 0).all()
 
 
-@pytest.mark.parametrize("B", [4, 8, 1024])
+@pytest.mark.parametrize("B", [4, 8, 16, 17, 136, 137, 1024])
 def test_n60_batched_scoring_against_oracle(gpu, oracle_n60, B):
-    """bn_score_orders at the bench's table on the oracle's entries: the few-order scan
-    (B = 4), the full-table scan (B = 8, 1,024; autotuned tiling) and the pruned table
-    give the same ranks and FP64 sums, and a sample of orders equals the oracle's
-    brute-force order score."""
+    """bn_score_orders at the bench's table on the oracle's entries: the scan of all
+    nodes' rank range with up to eight orders a thread (n * ceil(B / 8) <= 1,024 items:
+    B = 4, 8, 16 with several threads an item, B = 17 and 136 one thread an item, 136 in
+    1,024-thread blocks), the full-table scan (B = 137, 1,024; autotuned tiling) and the
+    pruned table give the same ranks and FP64 sums, and a sample of orders equals the
+    oracle's brute-force order score."""
     _, _, k, _, tab = oracle_n60
     orders = synth.random_orders(60, B, 1700 + B)
     full = gpu.table_from_scores(tab, k)

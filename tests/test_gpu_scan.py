@@ -22,16 +22,19 @@ def _check_shared(gpu, tab, k, orders, mode=None):
     return br, sc
 
 
-@pytest.mark.parametrize("B", [1, 2, 3, 5, 8, 17, 31, 33, 37, 256, 300])
+@pytest.mark.parametrize("B", [1, 2, 3, 5, 8, 17, 31, 33, 37, 256, 300, 1400])
 def test_shared_table_n6(gpu, B):
     data, arity, k, R, _ = synth.workload("n6_k2_m100")
     tab = oracle.build_table(data, arity, k, R=R)
     _check_shared(gpu, tab, k, synth.random_orders(6, B, B))
 
 
-@pytest.mark.parametrize("B", [1, 3, 9, 16, 97])
+@pytest.mark.parametrize("B", [1, 3, 9, 16, 51, 97, 409])
 def test_shared_table_n20_prior(gpu, B):
-    """Batches below 32 orders split each order's entries over the lanes of a warp."""
+    """Every dispatch of bn_score_orders: the scan of all nodes' rank range with R orders
+    a thread and T threads per (node, order group) item -- (T, R) = (8, 1), (8, 3), (4, 5),
+    (4, 8), (1, 8) in 256-thread blocks, (1, 8) with 260 items (a ragged last warp) -- and
+    the full-table scan once n * ceil(B / 8) exceeds 1,024 items (B = 409)."""
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     tab = oracle.build_table(data, arity, k, R=R)
     _check_shared(gpu, tab, k, synth.random_orders(20, B, 4 + B))

@@ -42,11 +42,13 @@ def test_noalloc_matches_score_orders_on_two_calls(gpu):
         assert np.array_equal(score, ref_score)
 
 
-@pytest.mark.parametrize("mode,B", [("full", 8), ("pruned", 64), ("unrank", 64)])
+@pytest.mark.parametrize("mode,B", [("full", 8), ("full", 97), ("full", 420), ("pruned", 64), ("unrank", 64)])
 def test_noalloc_every_scan_path(gpu, mode, B):
-    """The kernels the call can dispatch to: the few-order scan (n * B <= 256), the scan
-    over the pruned table's survivors and the scan that unranks parent sets on the fly;
-    two calls in a row, each equal to bn_score_orders on the same table and mode."""
+    """The kernels the call can dispatch to: the scan of all nodes' rank range with up to
+    eight orders a thread (n * ceil(B / 8) <= 1,024 items; B = 8 and 97 at n = 20), the
+    full-table scan (B = 420), the scan over the pruned table's survivors and the scan that
+    unranks parent sets on the fly; two calls in a row, each equal to bn_score_orders on
+    the same table and mode."""
     import torch
     bn = gpu
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
