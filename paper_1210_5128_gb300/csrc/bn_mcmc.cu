@@ -902,6 +902,416 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
     else chain_fused_body<false>(S, F, (int)c, lane, sm[warp], fcache);
 }
 
+// ---------------------------------------------------------------------------------
+// Speculative fused steps (cached networks, uniform proposal): SPEC_WARPS warps per chain.
+// Step t's proposal and uniform are Philox draws keyed by (t, chain), independent of the
+// state, so warp j evaluates step t + j -- the span walk, the exact fixed-point change and
+// the fast MH decision -- against the current state at the same time as the others, as if
+// steps t .. t + j - 1 were all rejected (a rejection leaves the state as it was).  The
+// first step that is not rejected ends the round: its warp applies it (a close call first
+// takes the exact FP64 test, on the state it applies to, and may turn out a rejection), the
+// evaluations after it are dropped, and the rejected steps before it only leave their
+// records.  Every decision, state and output is the one-warp kernel's (and the per-step
+// path's); with acceptance rate r a round commits 1 + (1 - r) + ... + (1 - r)^(W - 1)
+// steps for about the latency of one.
+// ---------------------------------------------------------------------------------
+static constexpr int SPEC_WARPS = 4;       // warps per chain
+static constexpr int SPEC_BATCH = 64;      // Philox draws prepared at a time
+
+struct SpecBatch {                         // steps base .. base + SPEC_BATCH - 1
+    uint8_t ra[SPEC_BATCH], rb[SPEC_BATCH];
+    double ru[SPEC_BATCH];
+    int64_t tlo[SPEC_BATCH], thi[SPEC_BATCH];
+};
+
+struct SpecChain {                         // the chain's running values (any warp commits)
+    double score, best;
+    long long Fcur, bestF, acc_count;
+    int dirty, bdirty, stale;
+    int dec[SPEC_WARPS];                   // 0 rejected, 1 accepted, 2 close call
+    int prog;
+};
+
+// step t's records: the traced score and accept flag, and the recorded state's edges
+__device__ __forceinline__ void spec_records(const ChainState& S, const FusedSmem& W, int c, int n, int64_t t,
+                                             double score, int acc, int lane)
+{
+    if (lane == 0 && t < S.trace_cap) {
+        S.trace_score[(size_t)c * S.trace_cap + t] = score;
+        S.trace_accept[(size_t)c * S.trace_cap + t] = (uint8_t)acc;
+    }
+    if (S.record_every > 0 && t >= S.burn_in && (t - S.burn_in) % S.record_every == 0) {
+        const int64_t ridx = (t - S.burn_in) / S.record_every;
+        if (ridx < S.record_cap)
+            for (int i = lane; i < n; i += 32) {
+                uint64_t m = S.pst[W.rank[i]];
+                while (m) {
+                    const int slot = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const int par = slot + (slot >= i ? 1 : 0);
+                    atomicOr((unsigned long long*)&S.rec_bits[(((size_t)c * n + i) * n + par) * S.rec_words + (ridx >> 6)],
+                             1ull << (ridx & 63));
+                }
+            }
+    }
+}
+
+template <bool JUMP>
+__device__ __forceinline__ void chain_spec_body(const ChainState& S, const FusedArgs& F, int c, int warp, int lane,
+                                                FusedSmem& W, SpecBatch& PB, SpecChain& K, const uint8_t* cache)
+{
+    const int n = S.n;
+    const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
+    const uint64_t* c_mask = (const uint64_t*)cache;
+    const int64_t* c_fx = (const int64_t*)(cache + 8 * (size_t)F.cap);
+    const uint64_t* c_orb = (const uint64_t*)(cache + 16 * (size_t)F.cap);
+    const uint32_t* c_rank = (const uint32_t*)(cache + 24 * (size_t)F.cap);
+    const uint32_t* c_off = (const uint32_t*)(cache + 28 * (size_t)F.cap);
+    if (warp == 0) {
+        for (int i = lane; i <= n; i += 32) W.coff[i] = c_off[i];
+        for (int i = lane; i < n; i += 32) {
+            W.ord[i] = S.cur_order[(size_t)c * n + i];
+            W.rank[i] = S.cur_rank[(size_t)c * n + i];
+            W.key[i] = S.cur_key[(size_t)c * n + i];
+            W.nkey[i] = W.key[i];
+            W.since[i] = F.t0;
+            W.brank[i] = S.best_rank[(size_t)c * n + i];
+            W.kst[i] = 0;
+            uint32_t cj;
+            for (cj = c_off[i]; cj + 1 < c_off[i + 1] && c_rank[cj] != W.rank[i]; ++cj) {}
+            W.cmask[i] = c_mask[cj];
+            W.corb[i] = c_orb[cj];
+            W.fx[i] = c_fx[cj];
+            W.cj[i] = cj;
+        }
+        __syncwarp();
+        uint64_t b0 = lane < n ? 1ull << W.ord[lane] : 0ull;
+        uint64_t b1 = lane + 32 < n ? 1ull << W.ord[lane + 32] : 0ull;
+        uint64_t s0 = b0, s1 = b1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t t0 = __shfl_up_sync(0xffffffffu, s0, off);
+            const uint64_t t1 = __shfl_up_sync(0xffffffffu, s1, off);
+            if (lane >= off) { s0 |= t0; s1 |= t1; }
+        }
+        const uint64_t first_half = __shfl_sync(0xffffffffu, s0, 31);
+        if (lane < n) W.pre[lane] = s0 & ~b0;
+        if (lane + 32 < n) W.pre[lane + 32] = (s1 | first_half) & ~b1;
+        long long Fcur = 0;
+        for (int i = lane; i < n; i += 32) Fcur += W.fx[i];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) Fcur += __shfl_xor_sync(0xffffffffu, Fcur, off);
+        if (lane == 0) {
+            K.score = S.cur_score[c];
+            K.best = S.best_score[c];
+            K.Fcur = Fcur;
+            K.bestF = isfinite(K.best) ? __double2ll_rn(K.best * 4294967296.0) : INT64_MIN / 4;
+            K.acc_count = 0;
+            K.dirty = K.bdirty = K.stale = 0;
+        }
+    }
+    __syncthreads();
+    const int64_t t_end = F.t0 + F.iters;
+    int64_t pbase = INT64_MIN / 2;         // step of PB's entry 0 (the same in every thread)
+    long long items = 0;                   // this warp's committed span lengths
+    for (int64_t t = F.t0; t < t_end;) {
+        if (t + SPEC_WARPS > pbase + SPEC_BATCH) {
+            // the next SPEC_BATCH steps' Philox blocks and what the MH test needs of them
+            // (u, and the fast test's fixed-point thresholds; see the one-warp kernel)
+            pbase = t;
+            for (int q = warp * 32 + lane; q < SPEC_BATCH; q += 32 * SPEC_WARPS) {
+                const U64x4 xr = philox4x64((uint64_t)(t + q), (uint64_t)c, 0, 0, S.seed, 0);
+                const double u = __dmul_rn(__dadd_rn((double)(xr.x[1] >> 12), 0.5), 0x1p-52);
+                const float luf = logf((float)u);
+                const double mg = 1e-6 * (1.0 + fabs((double)luf)) + F.margin_x;
+                const double to_fx = S.literal_log ? 4294967296.0 : 4294967296.0 / LN10;
+                int pa, pb;
+                pair_decode(n, __umul64hi(xr.x[0], P), pa, pb);
+                PB.ra[q] = (uint8_t)pa;
+                PB.rb[q] = (uint8_t)pb;
+                PB.ru[q] = u;
+                PB.tlo[q] = (int64_t)floor(((double)luf - mg) * to_fx) - 1;
+                PB.thi[q] = (int64_t)ceil(((double)luf + mg) * to_fx) + 1;
+            }
+            __syncthreads();
+        }
+        const int nact = (int)min((int64_t)SPEC_WARPS, t_end - t);
+        // ---- evaluation of step t + warp against the current state --------------------
+        const int64_t tj = t + warp;
+        const int q = (int)(tj - pbase);
+        int a = 0, b = 0, va = 0, vb = 0;
+        int node[2] = {-1, -1};
+        uint32_t nrank[2] = {0, 0}, wj[2] = {0, 0};
+        int64_t nfx[2] = {0, 0};
+        bool moved = false;
+        long long dfx = 0;
+        int exact = 1;
+        if (warp < nact) {
+            a = PB.ra[q];
+            b = PB.rb[q];
+            va = W.ord[a];
+            vb = W.ord[b];
+            const uint64_t bva = 1ull << va, bvb = 1ull << vb;
+            uint32_t wj1[2] = {0, 0}, cjv[2] = {0, 0};
+            uint64_t wnpc[2] = {0, 0};
+            bool act[2] = {false, false};
+            const int halves = b - a >= 32 ? 2 : 1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h >= halves) break;
+                const int p = a + lane + 32 * h;
+                if (p <= b) {
+                    const int nd = (p == a) ? vb : (p == b) ? va : W.ord[p];
+                    const uint64_t excl = (p == a) ? W.pre[a] : ((W.pre[p] & ~bva) | bvb);
+                    wnpc[h] = ~excl;
+                    node[h] = nd;
+                    const uint64_t old_pred = (p == a) ? W.pre[b] : (p == b) ? W.pre[a] : W.pre[p];
+                    const uint64_t gained = excl & ~old_pred;
+                    const uint32_t cj = W.cj[nd];
+                    cjv[h] = cj;
+                    const bool none_before = (W.corb[nd] & gained) == 0ull;
+                    const bool stays = (W.cmask[nd] & wnpc[h]) == 0ull;
+                    uint32_t restart = W.coff[nd];
+                    if (JUMP && !none_before && (gained & (gained - 1)) == 0ull)
+                        restart += F.gfirst[nd * 64 + (__ffsll((long long)gained) - 1)];
+                    wj[h] = none_before ? (stays ? cj : cj + 1) : restart;
+                    wj1[h] = W.coff[nd + 1];
+                    act[h] = !(none_before && stays);
+                }
+            }
+            span_walk(c_mask, wj, wj1, wnpc, act, lane, 64);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (node[h] < 0) continue;
+                nrank[h] = c_rank[wj[h]];
+                nfx[h] = c_fx[wj[h]];
+                moved |= wj[h] != cjv[h];
+                dfx += nfx[h] - W.fx[node[h]];
+            }
+            moved = __any_sync(0xffffffffu, moved);
+            if (moved) {
+                const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(dfx & 0x1fffff));
+                const unsigned mid = __reduce_add_sync(0xffffffffu, (unsigned)((dfx >> 21) & 0x1fffff));
+                const int hi = __reduce_add_sync(0xffffffffu, (int)(dfx >> 42));
+                dfx = (long long)hi * (1ll << 42) + (long long)mid * (1ll << 21) + (long long)lo;
+                exact = dfx < PB.tlo[q] ? 0 : (dfx > PB.thi[q] ? 1 : 2);
+            }
+            if (lane == 0) K.dec[warp] = exact;
+        }
+        __syncthreads();
+        // ---- the first step not rejected ends the round --------------------------------
+        int f = 0;
+        while (f < nact && K.dec[f] == 0) ++f;
+        // close calls: the exact FP64 test by that step's warp, on the current state
+        while (f < nact && K.dec[f] == 2) {
+            if (warp == f) {
+                if (K.stale) {
+                    refresh_keys(S, W, n, lane);
+                    if (lane == 0) K.stale = 0;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (node[h] >= 0) W.nkey[node[h]] = S.keys[(size_t)node[h] * S.Sp + nrank[h]];
+                __syncwarp();
+                double score = K.score;
+                if (K.dirty) score = seq_score(W.key, n, lane);
+                int acc = 0;
+                double s2 = 0.0;
+                if (lane == 0) {
+                    for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+                    const double delta = __dsub_rn(s2, score);
+                    const double lu = log(PB.ru[q]);
+                    acc = S.literal_log ? (lu < delta) : (lu < __dmul_rn(LN10, delta));
+                    K.score = score;
+                    K.dirty = 0;
+                    K.dec[f] = acc ? 3 : 0;             // 3: accepted, s' in W.nkey
+                }
+                acc = __shfl_sync(0xffffffffu, acc, 0);
+                if (!acc) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (node[h] >= 0) W.nkey[node[h]] = W.key[node[h]];
+                }
+            }
+            __syncthreads();
+            while (f < nact && K.dec[f] == 0) ++f;
+        }
+        const int prog = f < nact ? f + 1 : nact;
+        // ---- records and the accepted step --------------------------------------------
+        if (f < nact) {
+            if (warp == f) {
+                // the rejected steps before it, in order, on the state they saw
+                for (int j = 0; j < f; ++j) {
+                    spec_records(S, W, c, n, t + j, K.score, 0, lane);
+                    items += PB.rb[q - f + j] - PB.ra[q - f + j] + 1;
+                }
+                items += b - a + 1;
+                const uint64_t bva = 1ull << va, bvb = 1ull << vb;
+                double score = K.score, best = K.best;
+                long long Fcur = K.Fcur, bestF = K.bestF;
+                bool dirty = K.dirty, bdirty = K.bdirty, stale = K.stale;
+                const int d = K.dec[f];
+                bool lazy = false;
+                double s2 = score;
+                if (moved) {
+                    lazy = d == 1 && tj >= S.trace_cap;
+                    if (d == 1 && !lazy) {
+                        // an accepted traced step: its FP64 score s'
+                        if (stale) {
+                            refresh_keys(S, W, n, lane);
+                            stale = false;
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            if (node[h] >= 0) W.nkey[node[h]] = S.keys[(size_t)node[h] * S.Sp + nrank[h]];
+                        __syncwarp();
+                    }
+                    if (!lazy) {
+                        if (dirty) {
+                            score = seq_score(W.key, n, lane);
+                            dirty = false;
+                        }
+                        if (lane == 0) {
+                            s2 = 0.0;
+                            for (int i = 0; i < n; ++i) s2 = __dadd_rn(s2, key_to_double(W.nkey[i]));
+                        }
+                        s2 = __shfl_sync(0xffffffffu, s2, 0);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int nd = node[h];
+                        if (nd >= 0 && nrank[h] != W.rank[nd]) {
+                            credit_edges(S, c, nd, W.rank[nd], W.since[nd], tj);
+                            W.since[nd] = tj;
+                            W.rank[nd] = nrank[h];
+                            if (lazy) W.kst[nd] = 1;
+                            else W.key[nd] = W.nkey[nd];
+                            W.cj[nd] = wj[h];
+                            W.cmask[nd] = c_mask[wj[h]];
+                            W.corb[nd] = c_orb[wj[h]];
+                            W.fx[nd] = nfx[h];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && b - a <= 32) break;
+                    const int p = a + 1 + lane + 32 * h;
+                    if (p <= b) W.pre[p] = (W.pre[p] & ~bva) | bvb;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    W.ord[a] = (uint8_t)vb;
+                    W.ord[b] = (uint8_t)va;
+                }
+                __syncwarp();
+                bool newbest;
+                if (!moved) {
+                    newbest = false;                        // s' = s <= best
+                } else {
+                    Fcur += dfx;
+                    if (lazy) {
+                        dirty = true;
+                        stale = true;
+                    } else {
+                        score = s2;
+                    }
+                    const long long dd = Fcur - bestF;
+                    if (!dirty && !bdirty) {
+                        newbest = score > best;
+                    } else if (dd > F.guard_fx) {
+                        newbest = true;
+                    } else if (dd < -F.guard_fx) {
+                        newbest = false;
+                    } else if (__all_sync(0xffffffffu, (lane >= n || W.rank[lane] == W.brank[lane]) &&
+                                                           (lane + 32 >= n || W.rank[lane + 32] == W.brank[lane + 32]))) {
+                        newbest = false;
+                    } else {
+                        if (stale) {
+                            refresh_keys(S, W, n, lane);
+                            stale = false;
+                        }
+                        if (dirty) {
+                            score = seq_score(W.key, n, lane);
+                            dirty = false;
+                        }
+                        if (bdirty) {
+                            best = best_score_of(S, W, n, lane);
+                            bdirty = false;
+                        }
+                        newbest = score > best;
+                    }
+                }
+                if (newbest) {
+                    best = score;
+                    bdirty = dirty;
+                    bestF = Fcur;
+                    for (int i = lane; i < n; i += 32) {
+                        S.best_order[(size_t)c * n + i] = W.ord[i];
+                        S.best_rank[(size_t)c * n + i] = W.rank[i];
+                        W.brank[i] = W.rank[i];
+                    }
+                }
+                spec_records(S, W, c, n, tj, score, 1, lane);
+                if (lane == 0) {
+                    K.score = score;
+                    K.best = best;
+                    K.Fcur = Fcur;
+                    K.bestF = bestF;
+                    K.dirty = dirty;
+                    K.bdirty = bdirty;
+                    K.stale = stale;
+                    K.acc_count += 1;
+                }
+            }
+        } else if (warp < nact) {
+            // every step rejected: each warp its own records (the state is unchanged)
+            spec_records(S, W, c, n, tj, K.score, 0, lane);
+            items += b - a + 1;
+        }
+        __syncthreads();
+        t += prog;
+    }
+    if (lane == 0) atomicAdd((unsigned long long*)S.items_total, (unsigned long long)items);
+    if (warp == 0) {
+        __syncwarp();
+        double score = K.score, best = K.best;
+        if (K.stale) refresh_keys(S, W, n, lane);
+        if (K.dirty) score = seq_score(W.key, n, lane);
+        if (K.bdirty) best = best_score_of(S, W, n, lane);
+        for (int i = lane; i < n; i += 32) {
+            credit_edges(S, c, i, W.rank[i], W.since[i], t_end);
+            S.cur_order[(size_t)c * n + i] = W.ord[i];
+            S.cur_rank[(size_t)c * n + i] = W.rank[i];
+            S.cur_key[(size_t)c * n + i] = W.key[i];
+        }
+        if (lane == 0) {
+            S.cur_score[c] = score;
+            S.best_score[c] = best;
+            S.accepts[c] += K.acc_count;
+        }
+    }
+}
+
+// MODE 1: the network's survivors in the block's shared-memory cache; 2: the same layout
+// in global memory.  One chain per block.
+template <int MODE>
+__global__ void __launch_bounds__(32 * SPEC_WARPS) k_chain_spec(ChainState S, FusedArgs F)
+{
+    __shared__ FusedSmem W;
+    __shared__ SpecBatch PB;
+    __shared__ SpecChain K;
+    extern __shared__ __align__(16) uint8_t fcache[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x;
+    if (MODE == 1) {
+        fill_surv_cache(S, F, fcache, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    if (c >= S.C) return;                                  // block-uniform
+    chain_spec_body<MODE == 2>(S, F, c, warp, lane, W, PB, K, MODE == 2 ? F.gcache : fcache);
+}
+
 int build_survivor_cache(bn_table* t, cudaStream_t s)
 {
     // every pruned table whose entries fit the fixed point gets one (28 B per survivor):
@@ -933,6 +1343,7 @@ static int fused_smem_setup(int cap, size_t* smem)
     const size_t mx = surv_cache_stride(SURV_CAP_MAX);
     if (first_in_context(ctx)) {
         BN_CUDA(cudaFuncSetAttribute(k_chain_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        BN_CUDA(cudaFuncSetAttribute(k_chain_spec<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         BN_CUDA(cudaFuncSetAttribute(k_batch_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     }
     *smem = surv_cache_stride(cap);
@@ -1188,10 +1599,15 @@ static int fused_launch(bn_chains* ch, int64_t t0, int iters, cudaStream_t s, cu
     if (!F.staged) smem = 0;
     const unsigned grid = (unsigned)((ch->S.C + FUSED_WARPS - 1) / FUSED_WARPS);
     if (ev0) BN_CUDA(cudaEventRecord(ev0, s));
-    if (F.staged) k_chain_fused<1><<<grid, 32 * FUSED_WARPS, smem, s>>>(ch->S, F);
-    else if (F.gcache) k_chain_fused<2><<<grid, 32 * FUSED_WARPS, 0, s>>>(ch->S, F);
-    else k_chain_fused<0><<<grid, 32 * FUSED_WARPS, 0, s>>>(ch->S, F);
-    BN_LAUNCH_CHECK("k_chain_fused");
+    if (F.staged || F.gcache) {
+        // cached networks: several warps per chain evaluate consecutive steps at once
+        if (F.staged) k_chain_spec<1><<<(unsigned)ch->S.C, 32 * SPEC_WARPS, smem, s>>>(ch->S, F);
+        else k_chain_spec<2><<<(unsigned)ch->S.C, 32 * SPEC_WARPS, 0, s>>>(ch->S, F);
+        BN_LAUNCH_CHECK("k_chain_spec");
+    } else {
+        k_chain_fused<0><<<grid, 32 * FUSED_WARPS, 0, s>>>(ch->S, F);
+        BN_LAUNCH_CHECK("k_chain_fused");
+    }
     if (ev1) BN_CUDA(cudaEventRecord(ev1, s));
     k_step_advance<<<1, 1, 0, s>>>(ch->S, iters);
     BN_LAUNCH_CHECK("k_step_advance");
