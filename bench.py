@@ -209,10 +209,11 @@ def config_dict(chains, scan="pruned"):
 L2_FLUSH_BYTES = 512 << 20 # written, then another buffer read, between timed steps (L2 is 129 MB)
 SCORE_B = (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024)   # orders per bn_score_orders call in the scoring sweep
 ISSUE_PER_SM = 4           # warp schedulers per SM, one warp instruction per clock each
-# ncu smsp__inst_executed.sum of k_chain_fused<1> at this workload (256 chains, 1,000-step
-# launches), per chain per MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum
-# per launch of the full-table k_scan<1024,0> (256 items per node, the sampler's step)
-FUSED_INST_PER_CHAIN_STEP = 418.0
+# ncu smsp__inst_executed.sum of k_chain_spec<1> at this workload (256 chains, 1,000-step
+# launches; all four warps of a chain, the dropped speculative evaluations included), per
+# chain per committed MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum per
+# launch of the full-table k_scan<1024,0> (256 items per node, the sampler's step)
+FUSED_INST_PER_CHAIN_STEP = 713.0
 BUILD_INST_PER_ENTRY = 649.0     # ncu smsp__inst_executed.sum of k_build<4,1,0> per entry at n=60, m=1000
 SCAN_TRAFFIC_BYTES = 121.5e6
 
@@ -608,7 +609,7 @@ def main():
         # the fused sampler kernel, launch by launch (up to 1024 iterations per launch)
         fused_ms, fused_l = bn.chains_step_profiled(chains, max(ips, 256) * 4, stream=stream.cuda_stream)
         chains.free()
-        # the same kernel with one chain: one warp alone on the GPU, nothing competing for
+        # the same kernel with one chain: its block alone on the GPU, nothing competing for
         # its SM -- the dependent-latency floor of this code's MH step
         solo = bn.chains_create(table, 1, seed=seed + 99)
         bn.chains_step(solo, 2 * max(ips, 256), stream=stream.cuda_stream)
@@ -727,8 +728,8 @@ def main():
         iters_fused = max(ips, 256) * 4 / max(fused_l, 1)              # MH iterations per profiled launch
         inst = FUSED_INST_PER_CHAIN_STEP * args.chains * iters_fused   # warp instructions per launch
         issue_peak = n_sm * ISSUE_PER_SM * clock_mhz * 1e6
-        roof_head = {"kernel": "k_chain_fused<1> (the timed step: pruned table, one warp per chain, up to 1,024 "
-                               "MH iterations per launch)",
+        roof_head = {"kernel": "k_chain_spec<1> (the timed step: pruned table, four warps per chain evaluating "
+                               "consecutive MH steps at once, up to 1,024 MH iterations per launch)",
                      "bound": "alu", "unit": "warp instructions/s",
                      "achieved": inst / (avg_fused / 1000.0), "peak": issue_peak,
                      "frac": inst / (avg_fused / 1000.0) / issue_peak, "traffic": None,
@@ -740,14 +741,16 @@ def main():
                                     "us_per_iteration": 1000.0 * avg_fused / iters_fused},
                      "latency_floor": {"us_per_iteration_one_chain": 1000.0 * solo_ms / (max(ips, 256) * 4),
                                        "frac": (solo_ms / (max(ips, 256) * 4)) / (avg_fused / iters_fused),
-                                       "note": "the same kernel and table with a single chain (one warp alone on "
-                                               "the GPU): the dependent-latency floor of this MH step's code; frac = "
-                                               "floor / the 256-chain time per iteration"},
-                     "note": "latency-bound: 256 chains are 256 warps on 152 SMs, and each warp's MH step is a "
-                             "chain of dependent shared-memory loads, shuffles and votes, so issue slots stay "
-                             "idle; the instruction count per chain-iteration is ncu's smsp__inst_executed.sum "
-                             "for this kernel at this workload; DRAM traffic is the survivors' and chains' "
-                             "state only (the table stays in shared memory)"}
+                                       "note": "the same kernel and table with a single chain (one block of four "
+                                               "warps alone on the GPU): the dependent-latency floor of this MH "
+                                               "step's code; frac = floor / the 256-chain time per iteration"},
+                     "note": "latency-bound: 256 chains are 1,024 warps on 152 SMs; a round of a chain's four "
+                             "warps is a chain of dependent shared-memory loads, shuffles and votes, and ends at "
+                             "the slowest warp's evaluation and the accepted step's update (ncu: barrier and "
+                             "fixed-latency stalls lead), so issue slots stay idle; the instruction count per "
+                             "committed chain-iteration is ncu's smsp__inst_executed.sum for this kernel at this "
+                             "workload, speculative evaluations included; DRAM traffic is the survivors' and "
+                             "chains' state only (the table stays in shared memory)"}
         avg_full = scan_ms_full / max(scan_l_full, 1)
         tests = items_prof * S / max(scan_l_full, 1)                 # (entry, item) tests per launch
         roof_scan = {"kernel": "k_scan (full table, autotuned tiling, one launch per sampler step of all chains)",
@@ -812,7 +815,7 @@ def main():
                                      "on 4 B per (node, entry) + 8 B per entry, test fraction of the measured "
                                      "consistency-test peak; pruned_table: the same call once the table keeps "
                                      "only the entries no subset matches or beats (identical results)"},
-            "pruned_step": {"kernel": "k_chain_fused (up to 1024 MH iterations per launch, one warp per chain)",
+            "pruned_step": {"kernel": "k_chain_spec (up to 1024 MH iterations per launch, four warps per chain)",
                             "avg_ms_per_launch": avg_fused, "launches": fused_l,
                             "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
                             "survivors_per_node_mean": float(survivors.mean()),
