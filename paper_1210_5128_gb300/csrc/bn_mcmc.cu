@@ -924,6 +924,12 @@ struct SpecBatch {                         // steps base .. base + SPEC_BATCH - 
     int64_t tlo[SPEC_BATCH], thi[SPEC_BATCH];
 };
 
+struct SpecTasks {                         // a round's re-scoring walks, shared by the warps
+    uint32_t js[SPEC_WARPS][MAXN], je[SPEC_WARPS][MAXN], hit[SPEC_WARPS][MAXN];
+    uint64_t np[SPEC_WARPS][MAXN];
+    int cnt[SPEC_WARPS];
+};
+
 struct SpecChain {                         // the chain's running values (any warp commits)
     double score, best;
     long long Fcur, bestF, acc_count;
@@ -958,7 +964,8 @@ __device__ __forceinline__ void spec_records(const ChainState& S, const FusedSme
 
 template <bool JUMP>
 __device__ __forceinline__ void chain_spec_body(const ChainState& S, const FusedArgs& F, int c, int warp, int lane,
-                                                FusedSmem& W, SpecBatch& PB, SpecChain& K, const uint8_t* cache)
+                                                FusedSmem& W, SpecBatch& PB, SpecChain& K, SpecTasks& TK,
+                                                const uint8_t* cache)
 {
     const int n = S.n;
     const uint64_t P = (uint64_t)n * (uint64_t)(n - 1) / 2;
@@ -1046,15 +1053,15 @@ __device__ __forceinline__ void chain_spec_body(const ChainState& S, const Fused
         bool moved = false;
         long long dfx = 0;
         int exact = 1;
+        uint32_t wj1[2] = {0, 0}, cjv[2] = {0, 0};
+        uint64_t wnpc[2] = {0, 0};
+        bool act[2] = {false, false};
         if (warp < nact) {
             a = PB.ra[q];
             b = PB.rb[q];
             va = W.ord[a];
             vb = W.ord[b];
             const uint64_t bva = 1ull << va, bvb = 1ull << vb;
-            uint32_t wj1[2] = {0, 0}, cjv[2] = {0, 0};
-            uint64_t wnpc[2] = {0, 0};
-            bool act[2] = {false, false};
             const int halves = b - a >= 32 ? 2 : 1;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -1079,7 +1086,48 @@ __device__ __forceinline__ void chain_spec_body(const ChainState& S, const Fused
                     act[h] = !(none_before && stays);
                 }
             }
-            span_walk(c_mask, wj, wj1, wnpc, act, lane, 64);
+        }
+        // the round's re-scoring walks (the nodes that cannot keep their parent sets, ~3 a
+        // step) are shared by the four warps, so a step with many of them does not hold the
+        // round back: each warp posts its own, all walk them in turn, each takes its answers
+        int ti[2] = {0, 0};
+        {
+            const unsigned m0 = __ballot_sync(0xffffffffu, act[0]), m1 = __ballot_sync(0xffffffffu, act[1]);
+            const unsigned lt = (1u << lane) - 1u;
+            ti[0] = __popc(m0 & lt);
+            ti[1] = __popc(m0) + __popc(m1 & lt);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (act[h]) {
+                    TK.js[warp][ti[h]] = wj[h];
+                    TK.je[warp][ti[h]] = wj1[h];
+                    TK.np[warp][ti[h]] = wnpc[h];
+                }
+            if (lane == 0) TK.cnt[warp] = __popc(m0) + __popc(m1);
+        }
+        __syncthreads();
+        {
+            int base[SPEC_WARPS + 1];
+            base[0] = 0;
+#pragma unroll
+            for (int w = 0; w < SPEC_WARPS; ++w) base[w + 1] = base[w] + TK.cnt[w];
+            for (int g = warp; g < base[SPEC_WARPS]; g += SPEC_WARPS) {
+                int w = 0, i = g;
+#pragma unroll
+                for (int x = 1; x < SPEC_WARPS; ++x)
+                    if (g >= base[x]) {
+                        w = x;
+                        i = g - base[x];
+                    }
+                const uint32_t hit = warp_walk(c_mask, TK.js[w][i], TK.je[w][i], TK.np[w][i], lane);
+                if (lane == 0) TK.hit[w][i] = hit;
+            }
+        }
+        __syncthreads();
+        if (warp < nact) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (act[h]) wj[h] = TK.hit[warp][ti[h]];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (node[h] < 0) continue;
@@ -1296,11 +1344,12 @@ __device__ __forceinline__ void chain_spec_body(const ChainState& S, const Fused
 // MODE 1: the network's survivors in the block's shared-memory cache; 2: the same layout
 // in global memory.  One chain per block.
 template <int MODE>
-__global__ void __launch_bounds__(32 * SPEC_WARPS) k_chain_spec(ChainState S, FusedArgs F)
+__global__ void __launch_bounds__(32 * SPEC_WARPS, 1) k_chain_spec(ChainState S, FusedArgs F)
 {
     __shared__ FusedSmem W;
     __shared__ SpecBatch PB;
     __shared__ SpecChain K;
+    __shared__ SpecTasks TK;
     extern __shared__ __align__(16) uint8_t fcache[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x;
@@ -1309,7 +1358,7 @@ __global__ void __launch_bounds__(32 * SPEC_WARPS) k_chain_spec(ChainState S, Fu
         __syncthreads();
     }
     if (c >= S.C) return;                                  // block-uniform
-    chain_spec_body<MODE == 2>(S, F, c, warp, lane, W, PB, K, MODE == 2 ? F.gcache : fcache);
+    chain_spec_body<MODE == 2>(S, F, c, warp, lane, W, PB, K, TK, MODE == 2 ? F.gcache : fcache);
 }
 
 int build_survivor_cache(bn_table* t, cudaStream_t s)
