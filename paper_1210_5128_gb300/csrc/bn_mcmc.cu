@@ -962,6 +962,22 @@ __device__ __forceinline__ void spec_records(const ChainState& S, const FusedSme
     }
 }
 
+// credit_edges for a parent set given in node space (bit u: parent u), as the survivor
+// cache holds it -- no read of the parent-set table
+__device__ __forceinline__ void credit_edges_nodes(const ChainState& S, int c, int v, uint64_t m, int64_t from,
+                                                   int64_t to)
+{
+    const int64_t lo = max(from, S.burn_in);
+    if (to <= lo) return;
+    const uint32_t d = (uint32_t)(to - lo);
+    uint32_t* E = S.edge + ((size_t)c * S.n + v) * S.n;
+    while (m) {
+        const int u = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        atomicAdd(&E[u], d);
+    }
+}
+
 template <bool JUMP>
 __device__ __forceinline__ void chain_spec_body(const ChainState& S, const FusedArgs& F, int c, int warp, int lane,
                                                 FusedSmem& W, SpecBatch& PB, SpecChain& K, SpecTasks& TK,
@@ -1229,7 +1245,7 @@ __device__ __forceinline__ void chain_spec_body(const ChainState& S, const Fused
                     for (int h = 0; h < 2; ++h) {
                         const int nd = node[h];
                         if (nd >= 0 && nrank[h] != W.rank[nd]) {
-                            credit_edges(S, c, nd, W.rank[nd], W.since[nd], tj);
+                            credit_edges_nodes(S, c, nd, W.cmask[nd], W.since[nd], tj);
                             W.since[nd] = tj;
                             W.rank[nd] = nrank[h];
                             if (lazy) W.kst[nd] = 1;
