@@ -189,10 +189,25 @@ int bn_score_orders_noalloc(const bn_table* t, const uint8_t* orders, int B,
  *                   its rank on the fly (the paper's first strategy, Sec. V.B / Algorithm
  *                   2, in this library's size-ascending combinatorial number system)
  *                   instead of read from the parent-set table.  Results are identical. 
- * Errors: BN_EINVAL, BN_ENOMEM, BN_EUNSUPPORTED, BN_ECUDA. */
+ *   BN_SCAN_SLICED  every entry, as BN_SCAN_FULL, with the orders bit-sliced (k <= 4):
+ *                   a node's entries are visited in score order (each entry's parent
+ *                   nodes, a byte apiece, 4 B per entry from HBM) and for every group of
+ *                   32 orders one word per parent node says in which of them that node
+ *                   precedes the scored one; the AND of at most four such words tests an
+ *                   entry against 32 orders, and an order takes the first consistent
+ *                   entry, which is the (max score, lowest rank) one.  Results are
+ *                   identical.
+ *   BN_SCAN_SORTED  BN_SCAN_SLICED that stops early: no entry ranked below the empty
+ *                   set (consistent with every order) is read, and a tile of orders
+ *                   stops reading a node's entries once every order has its first
+ *                   consistent one.  Results are identical.
+ * Errors: BN_EINVAL (unknown mode), BN_ENOMEM, BN_EUNSUPPORTED (the sliced modes with
+ * k > 4), BN_ECUDA. */
 #define BN_SCAN_FULL   0
 #define BN_SCAN_PRUNED 1
 #define BN_SCAN_UNRANK 2
+#define BN_SCAN_SLICED 3
+#define BN_SCAN_SORTED 4
 int bn_table_set_scan(bn_table* t, int mode, void* stream);
 /* surviving entries per node after pruning (n int64) */
 int bn_table_pruned(const bn_table* t, int64_t* survivors_per_node);

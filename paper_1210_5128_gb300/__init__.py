@@ -359,11 +359,12 @@ def score_orders_sum(t: Table, orders):
     return sc, ns
 
 
-SCAN_FULL, SCAN_PRUNED, SCAN_UNRANK = 0, 1, 2
+SCAN_FULL, SCAN_PRUNED, SCAN_UNRANK, SCAN_SLICED, SCAN_SORTED = 0, 1, 2, 3, 4
 
 
 def table_set_scan(t: Table, mode: int):
-    """Full-table scan or the scan over entries no subset dominates (bn_table_set_scan)."""
+    """Scan mode of a table (bn_table_set_scan): SCAN_FULL, SCAN_PRUNED, SCAN_UNRANK,
+    SCAN_SLICED or SCAN_SORTED."""
     _check(lib().bn_table_set_scan(t.handle, mode, None))
 
 

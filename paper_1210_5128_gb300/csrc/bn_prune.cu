@@ -326,8 +326,11 @@ extern "C" int bn_table_set_scan(bn_table* t, int mode, void* stream)
 {
     set_error(BN_OK, "");
     if (!t) return set_error(BN_EINVAL, "bn_table_set_scan: NULL table");
-    if (mode != BN_SCAN_FULL && mode != BN_SCAN_PRUNED && mode != BN_SCAN_UNRANK)
+    if (mode != BN_SCAN_FULL && mode != BN_SCAN_PRUNED && mode != BN_SCAN_UNRANK && mode != BN_SCAN_SLICED &&
+        mode != BN_SCAN_SORTED)
         return set_error(BN_EINVAL, "bn_table_set_scan: mode %d", mode);
+    if ((mode == BN_SCAN_SLICED || mode == BN_SCAN_SORTED) && !t->sset)
+        return set_error(BN_EUNSUPPORTED, "bn_table_set_scan: the bit-sliced scans need k <= 4 (k = %d)", t->k);
     if (mode == BN_SCAN_PRUNED) {
         int rc = prune_table(t, (cudaStream_t)stream);
         if (rc) return rc;

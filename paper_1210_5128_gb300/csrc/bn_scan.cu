@@ -349,6 +349,8 @@ int launch_scan(const bn_table* t, const ScanPlan& pl, const uint32_t* list_coun
                 uint32_t* list_best, int cap, uint32_t* status, cudaStream_t s)
 {
     if (t->scan_mode == BN_SCAN_PRUNED) return launch_scan_pruned(t, list_count, list_pc, list_best, cap, s);
+    if (t->scan_mode == BN_SCAN_SLICED || t->scan_mode == BN_SCAN_SORTED)
+        return launch_scan_sliced(t, list_count, list_pc, list_best, cap, t->scan_mode == BN_SCAN_SORTED, status, s);
     ScanArgs A;
     A.spos = t->spos;
     A.pst = t->pst;
@@ -650,7 +652,7 @@ __global__ void k_reduce_orders(const uint32_t* __restrict__ list_best, const ui
 // the environment keeps the fixed plan.
 int ensure_tuned(const bn_table* t, int max_items, cudaStream_t s)
 {
-    if (!t || t->scan_mode == BN_SCAN_PRUNED || max_items < 1) return BN_OK;
+    if (!t || (t->scan_mode != BN_SCAN_FULL && t->scan_mode != BN_SCAN_UNRANK) || max_items < 1) return BN_OK;
     const int groups = (max_items + SCAN_THREADS - 1) / SCAN_THREADS;
     if (groups > 8 || t->tuned_sub[groups]) return BN_OK;
     static const bool off = [] {

@@ -264,7 +264,7 @@ int rank_entries(bn_table* t, cudaStream_t s)
     k_spos_transpose<<<dim3((unsigned)(t->Sp / 32), (unsigned)((t->n + 31) / 32)), dim3(32, 8), 0, s>>>(t->spos, t->n, t->Sp,
                                                                                                     t->spos_t);
     BN_LAUNCH_CHECK("k_spos_transpose");
-    return BN_OK;
+    return build_sset(t, s);
 }
 
 }  // namespace bn

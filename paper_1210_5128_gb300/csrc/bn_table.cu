@@ -899,6 +899,7 @@ extern "C" void bn_table_free(bn_table* t)
     cudaFree(t->spos);
     cudaFree(t->srank);
     cudaFree(t->spos_t);
+    cudaFree(t->sset);
     cudaFree(t->alive_block);
     cudaFree(t->gcache);
     delete t;

@@ -14,8 +14,13 @@ struct bn_table {
                                // ordered by score descending, rank ascending (padding: ~0)
     uint32_t* srank = nullptr; // [n][Sp] inverse of spos: rank at sorted position p
     uint32_t* spos_t = nullptr;// [Sp / 2][n][2] spos entry-major, rank pairs side by side (k_scan_nodes)
+    uint32_t* sset = nullptr;  // [n][sset_stride] parent node ids (a byte each) of the entry at each
+                               // sorted position, k <= 4 only (bn_sliced.cu); null otherwise
+    int64_t sset_stride = 0;   // S rounded up to whole stages of the sliced scan
+    uint32_t cut[64] = {0};    // per node: sorted position of the empty set + 1 (host copy); no
+                               // entry at or past it can be a node's best
     size_t bytes = 0;
-    int scan_mode = 0;         // BN_SCAN_FULL, BN_SCAN_PRUNED or BN_SCAN_UNRANK
+    int scan_mode = 0;         // BN_SCAN_FULL, _PRUNED, _UNRANK, _SLICED or _SORTED
     // entries not dominated by a proper subset, per node in sorted-position order
     // (bn_prune.cu): candidate masks and sorted positions, node offsets and counts
     uint64_t* amask = nullptr;
@@ -42,6 +47,13 @@ namespace bn {
 
 // Sorted positions and their inverse for every node (bn_sort.cu).
 int rank_entries(bn_table* t, cudaStream_t s);
+
+// The bit-sliced scans (bn_sliced.cu): the parent sets in sorted-position order (k <= 4;
+// nothing for larger k), and the scan of work lists in the layout of launch_scan, as a
+// full pass (cut = false) or stopping early with identical results (cut = true).
+int build_sset(bn_table* t, cudaStream_t s);
+int launch_scan_sliced(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc, uint32_t* list_best,
+                       int cap, bool cut, uint32_t* status, cudaStream_t s);
 
 // Dominance pruning and the scan over the surviving entries (bn_prune.cu).
 int prune_table(bn_table* t, cudaStream_t s);

@@ -42,18 +42,20 @@ def test_noalloc_matches_score_orders_on_two_calls(gpu):
         assert np.array_equal(score, ref_score)
 
 
-@pytest.mark.parametrize("mode,B", [("full", 8), ("full", 97), ("full", 420), ("pruned", 64), ("unrank", 64)])
+@pytest.mark.parametrize("mode,B", [("full", 8), ("full", 97), ("full", 420), ("pruned", 64), ("unrank", 64),
+                                    ("sliced", 64), ("sorted", 300)])
 def test_noalloc_every_scan_path(gpu, mode, B):
     """The kernels the call can dispatch to: the scan of all nodes' rank range with up to
     eight orders a thread (n * ceil(B / 8) <= 1,024 items; B = 8 and 97 at n = 20), the
-    full-table scan (B = 420), the scan over the pruned table's survivors and the scan that
-    unranks parent sets on the fly; two calls in a row, each equal to bn_score_orders on
-    the same table and mode."""
+    full-table scan (B = 420), the scan over the pruned table's survivors, the scan that
+    unranks parent sets on the fly and the two bit-sliced scans; two calls in a row, each
+    equal to bn_score_orders on the same table and mode."""
     import torch
     bn = gpu
     data, arity, k, R, _ = synth.workload("n20_k4_m1000")
     t = bn.build_scores(data, arity, k, R=R)
-    bn.table_set_scan(t, {"full": bn.SCAN_FULL, "pruned": bn.SCAN_PRUNED, "unrank": bn.SCAN_UNRANK}[mode])
+    bn.table_set_scan(t, {"full": bn.SCAN_FULL, "pruned": bn.SCAN_PRUNED, "unrank": bn.SCAN_UNRANK,
+                          "sliced": bn.SCAN_SLICED, "sorted": bn.SCAN_SORTED}[mode])
     for seed in (5, 6):
         orders = synth.random_orders(20, B, seed)
         ref_rank, ref_score = bn.score_orders(t, orders)
