@@ -208,14 +208,17 @@ def config_dict(chains, scan="pruned"):
 
 L2_FLUSH_BYTES = 512 << 20 # written, then another buffer read, between timed steps (L2 is 129 MB)
 SCORE_B = (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024)   # orders per bn_score_orders call in the scoring sweep
+SLICED_B = (1, 4, 16, 32, 64, 128, 256, 1024, 4096)  # the same for the bit-sliced scans
 ISSUE_PER_SM = 4           # warp schedulers per SM, one warp instruction per clock each
 # ncu smsp__inst_executed.sum of k_chain_spec<1> at this workload (256 chains, 1,000-step
 # launches; all four warps of a chain, the dropped speculative evaluations included), per
 # chain per committed MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum per
 # launch of the full-table k_scan<1024,0> (256 items per node, the sampler's step)
-FUSED_INST_PER_CHAIN_STEP = 713.0
+FUSED_INST_PER_CHAIN_STEP = 789.0
+FUSED_TRAFFIC_BYTES = 2.142e6    # ncu dram bytes read + written per 1,000-step launch of k_chain_spec<1>
 BUILD_INST_PER_ENTRY = 649.0     # ncu smsp__inst_executed.sum of k_build<4,1,0> per entry at n=60, m=1000
 SCAN_TRAFFIC_BYTES = 121.5e6
+SLICED_TRAFFIC_BYTES = None      # ncu dram bytes per launch of k_scan_sliced at the roofline's batch
 
 
 def _flush_l2(torch, flush, stream):
@@ -520,28 +523,54 @@ def main():
     # ---- bn_score_orders on a few orders: the full-table scan at memory speed -------------
     #      (the paper scores one order per MH iteration); device time of the scan kernel by
     #      CUDA events around its launch, L2 flushed before every call
-    hbm_leg = []
     flush = (torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev),
              torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev))
     hbm_bytes = 4 * n * S + 8 * S            # sorted positions of every entry + the mask table once
+    sliced_bytes = 4 * n * S                 # the parent-node bytes of every entry, in score order
     test_rate = bn.measure_test_rate()       # measured peak of the scan's consistency test
-    for B in SCORE_B:
-        orders = torch.from_numpy(synth.random_orders(n, B, 100 + B)).to(dev)
-        for _ in range(3):
-            bn.score_orders_profiled(table, orders)
-        times = []
-        for _ in range(10 if B <= 64 else 5):
-            _flush_l2(torch, flush, torch.cuda.current_stream())
-            torch.cuda.synchronize()
-            times.append(1000.0 * bn.score_orders_profiled(table, orders)[2])
-        us = float(np.median(times))
-        tests = float(n) * S * B                 # (entry, order) consistency tests of one pass
-        hbm_leg.append({"orders": B, "kernel": "k_scan_nodes" if n * ((B + 7) // 8) <= 1024 else "k_scan",
-                        "scan_us": us, "scan_us_mean": float(np.mean(times)), "calls": len(times),
-                        "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9,
-                        "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak,
-                        "tests_per_s": tests / (us / 1e6), "test_frac": tests / (us / 1e6) / test_rate,
+    # entries above (and including) each node's empty set in score order: all the sorted
+    # mode can read
+    tab_host = bn.table_scores(table)
+    cut_entries = int(sum(int((tab_host[i] > tab_host[i, 0]).sum()) + 1 for i in range(n)))
+    del tab_host
+
+    def score_sweep(mode, batches):
+        bn.table_set_scan(table, mode)
+        out = []
+        for B in batches:
+            orders = torch.from_numpy(synth.random_orders(n, B, 100 + B)).to(dev)
+            for _ in range(3):
+                bn.score_orders_profiled(table, orders)
+            times = []
+            for _ in range(10 if B <= 64 else 5):
+                _flush_l2(torch, flush, torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                times.append(1000.0 * bn.score_orders_profiled(table, orders)[2])
+            us = float(np.median(times))
+            out.append({"orders": B, "scan_us": us, "scan_us_mean": float(np.mean(times)), "calls": len(times),
                         "order_evals_per_s": B / (us / 1e6)})
+        bn.table_set_scan(table, bn.SCAN_FULL)
+        return out
+
+    hbm_leg = score_sweep(bn.SCAN_FULL, SCORE_B)
+    for x in hbm_leg:
+        B, us = x["orders"], x["scan_us"]
+        tests = float(n) * S * B                 # (entry, order) consistency tests of one pass
+        x.update({"kernel": "k_scan_nodes" if n * ((B + 7) // 8) <= 1024 else "k_scan",
+                  "achieved_gbs": hbm_bytes / (us / 1e6) / 1e9, "frac": hbm_bytes / (us / 1e6) / 1e9 / hbm_peak,
+                  "tests_per_s": tests / (us / 1e6), "test_frac": tests / (us / 1e6) / test_rate})
+    sliced_leg = score_sweep(bn.SCAN_SLICED, SLICED_B)
+    for x in sliced_leg:
+        us = x["scan_us"]
+        x.update({"kernel": "k_scan_sliced", "achieved_gbs": sliced_bytes / (us / 1e6) / 1e9,
+                  "frac": sliced_bytes / (us / 1e6) / 1e9 / hbm_peak,
+                  "tests_per_s": float(n) * S * x["orders"] / (us / 1e6)})
+    sorted_leg = score_sweep(bn.SCAN_SORTED, SLICED_B)
+    for x in sorted_leg:
+        x.update({"kernel": "k_scan_sliced (early exit)", "entries_at_most": cut_entries})
+    roof_b = max(x["orders"] for x in sliced_leg if x["frac"] >= 0.7) if any(
+        x["frac"] >= 0.7 for x in sliced_leg) else sliced_leg[0]["orders"]
+    roof_sl = next(x for x in sliced_leg if x["orders"] == roof_b)
 
     # ---- the sum-based order score of the prior scorer (Sec. III.B) on the same table:
     #      one order, whole-call device time, L2 flushed before every call ------------------
@@ -584,6 +613,17 @@ def main():
         unr_steps = max(3, min(args.steps, 50))
         ms_unr = _timed(bn, torch, unr, unr_steps, stream, pieces=unr_steps, flush=flush)
         unr.free()
+        # ---- the same steps on the bit-sliced scans: every entry, and stopping early -------
+        sl_samp = {}
+        for name, mode in (("sliced", bn.SCAN_SLICED), ("sorted", bn.SCAN_SORTED)):
+            bn.table_set_scan(table, mode)
+            chs = bn.chains_create(table, args.chains, seed=seed)
+            bn.chains_step(chs, args.warmup, stream=stream.cuda_stream)
+            ms_sl = _timed(bn, torch, chs, args.steps, stream, pieces=args.steps, flush=flush)
+            sl_ms, sl_l = bn.chains_step_profiled(chs, prof_steps, stream=stream.cuda_stream)
+            chs.free()
+            sl_samp[name] = {"value": world * args.chains * args.steps / (ms_sl / 1000.0),
+                             "ms_per_step": ms_sl / args.steps, "scan_avg_ms": sl_ms / max(sl_l, 1)}
         bn.table_set_scan(table, bn.SCAN_FULL)
 
         # ---- pruned scan sampler (headline) ----------------------------------------------
@@ -732,7 +772,7 @@ def main():
                                "consecutive MH steps at once, up to 1,024 MH iterations per launch)",
                      "bound": "alu", "unit": "warp instructions/s",
                      "achieved": inst / (avg_fused / 1000.0), "peak": issue_peak,
-                     "frac": inst / (avg_fused / 1000.0) / issue_peak, "traffic": None,
+                     "frac": inst / (avg_fused / 1000.0) / issue_peak, "traffic": FUSED_TRAFFIC_BYTES,
                      "peak_source": f"derived: {n_sm} SMs x {ISSUE_PER_SM} schedulers x 1 warp instruction per "
                                     f"clock x {clock_mhz:.0f} MHz (SM clock sampled in the timed region)",
                      "per_launch": {"avg_ms": avg_fused, "launches": fused_l, "iterations": iters_fused,
@@ -805,16 +845,29 @@ def main():
                                "note": "issue-bound: warp instructions per entry = ncu smsp__inst_executed.sum of "
                                        "this kernel at this workload (649); peak as for roofline; DRAM carries only "
                                        "the 8 B written per entry"},
-            "roofline_hbm": {"kernel": "k_scan_nodes (bn_score_orders, full table, one order)", "bound": "hbm",
-                             "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                             "frac": hbm_leg[0]["frac"], "traffic": None, "peak_source": peak_src,
-                             "bytes_algorithmic": hbm_bytes},
-            "score_orders": {"by_orders": hbm_leg, "test_rate_peak": test_rate, "pruned_table": pruned_scoring,
+            "roofline_hbm": {"kernel": f"k_scan_sliced (bn_score_orders, BN_SCAN_SLICED: every entry of the full "
+                                       f"table, {roof_b} orders)", "bound": "hbm",
+                             "achieved": roof_sl["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                             "frac": roof_sl["frac"], "traffic": SLICED_TRAFFIC_BYTES, "peak_source": peak_src,
+                             "bytes_algorithmic": sliced_bytes, "orders": roof_b,
+                             "note": "the largest batch of the sweep at which the full pass stays at or above 0.7 of "
+                                     "HBM; algorithmic bytes = 4 B (the parent-node bytes) per (node, entry); "
+                                     "traffic = ncu dram bytes read + written for this launch shape"},
+            "roofline_hbm_one_order": {"kernel": "k_scan_nodes (bn_score_orders, BN_SCAN_FULL, one order)",
+                                       "bound": "hbm", "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak,
+                                       "unit": "GB/s", "frac": hbm_leg[0]["frac"], "bytes_algorithmic": hbm_bytes},
+            "score_orders": {"by_orders": hbm_leg, "sliced": sliced_leg, "sorted": sorted_leg,
+                             "test_rate_peak": test_rate, "pruned_table": pruned_scoring,
                              "note": "bn_score_orders on B random orders of the full n=60 table: scan kernel time "
-                                     "(CUDA events around its launch, L2 flushed before every call); HBM fraction "
-                                     "on 4 B per (node, entry) + 8 B per entry, test fraction of the measured "
-                                     "consistency-test peak; pruned_table: the same call once the table keeps "
-                                     "only the entries no subset matches or beats (identical results)"},
+                                     "(CUDA events around its launch, L2 flushed before every call). by_orders: "
+                                     "BN_SCAN_FULL (one 64-bit mask test per entry and order), HBM fraction on 4 B "
+                                     "per (node, entry) + 8 B per entry, test fraction of the measured "
+                                     "consistency-test peak; sliced: BN_SCAN_SLICED (entries in score order, 32 "
+                                     "orders per AND of parent words; every entry read), HBM fraction on 4 B per "
+                                     "(node, entry); sorted: BN_SCAN_SORTED (the same, nothing below the empty set "
+                                     "read, stopping once every order has its entry; entries_at_most = the entries "
+                                     "above the empty sets); pruned_table: the table keeping only the entries no "
+                                     "subset matches or beats. All modes give identical results"},
             "pruned_step": {"kernel": "k_chain_spec (up to 1024 MH iterations per launch, four warps per chain)",
                             "avg_ms_per_launch": avg_fused, "launches": fused_l,
                             "us_per_iteration": 1000.0 * fused_ms / max(ips, 256) / 4,
@@ -823,6 +876,8 @@ def main():
                             "survivor_fraction": float(survivors.sum() / (n * S)), "prune_s": prune_s},
             "full_scan": {"value": world * args.chains * args.steps / (ms_full / 1000.0),
                           "ms_per_step": ms_full / args.steps, "items_per_step": items_full / args.steps,
+                          "sliced": dict(sl_samp["sliced"], note="BN_SCAN_SLICED: the bit-sliced full pass"),
+                          "sorted": dict(sl_samp["sorted"], note="BN_SCAN_SORTED: bit-sliced, stopping early"),
                           "unranked_sets": {"value": world * args.chains * unr_steps / (ms_unr / 1000.0),
                                             "ms_per_step": ms_unr / unr_steps, "steps": unr_steps,
                                             "note": "BN_SCAN_UNRANK: every parent set computed from its rank "
