@@ -56,8 +56,7 @@ __host__ __device__ constexpr size_t sl_smem(int G)
            + (size_t)32 * G * 4                      // per-item best sorted position
            + 16 * SL_STAGES + 64;                    // full/empty mbarriers, flags, skip words
 }
-// all shared memory of a block
-__host__ __device__ constexpr size_t sl_smem_total(int G) { return sl_smem(G) + (sl_static_p(G) ? sl_p_bytes(G) : 0); }
+
 
 struct SlicedArgs {
     const uint32_t* sset;          // [n][Ssp] parent node ids of the entry at each sorted position
@@ -146,6 +145,9 @@ __device__ __forceinline__ int Pw(int g, int v)
 template <int G, bool CUT>
 __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
 {
+    // one record per item and step (measured: faster everywhere but in the full pass over
+    // eight groups, where hits are sparse and the prefix ORs cost more than the duplicates)
+    constexpr bool DEDUP = CUT || G <= 4;
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t* s_ent = (uint32_t*)smem;                                            // [STAGES][SUB]
     // P[v][g] for lane l at word (g / 2) * ROWS * 64 + v * 64 + (g % 2) * 32 + l: a row of
@@ -317,16 +319,31 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
 #pragma unroll
                     for (int g = 0; g < G; ++g) any |= raw[g] & ~found[g];
                     if (__any_sync(0xffffffffu, any != 0)) {
-                        // rare: the lane's entries again, one at a time, recording new items
                         const uint32_t pos0 = (uint32_t)(base + q * 128 + 4 * lane);
+                        if constexpr (DEDUP) {
+                            // rare: record the step's new items.  Positions run lane-major
+                            // (lane l holds pos0 .. pos0 + 3), so of the lanes hitting an
+                            // item only the lowest records it (an exclusive prefix OR over
+                            // the lanes), at its first entry that hits: one atomicMin per
+                            // item and step, however densely the top of a node's list
+                            // matches the orders
 #pragma unroll
-                        for (int g = 0; g < G; ++g) {
-                            uint32_t hit = raw[g] & ~found[g];
-                            if (hit) {
+                            for (int g = 0; g < G; ++g) {
+                                const uint32_t hit = raw[g] & ~found[g];
+                                uint32_t incl = hit;
+#pragma unroll
+                                for (int d = 1; d < 32; d <<= 1) {
+                                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                                    if (lane >= d) incl |= y;
+                                }
+                                const uint32_t before = __shfl_up_sync(0xffffffffu, incl, 1);   // lanes below
+                                uint32_t mine = lane == 0 ? hit : hit & ~before;
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
+                                    if (!mine) break;
                                     uint32_t m = word(w[u], 0x5504, g) & word(w[u], 0x5514, g) &
-                                                 word(w[u], 0x5524, g) & word(w[u], 0x5534, g) & ~found[g];
+                                                 word(w[u], 0x5524, g) & word(w[u], 0x5534, g) & mine;
+                                    mine &= ~m;
                                     while (m) {
                                         const int b = __ffs(m) - 1;
                                         m &= m - 1;
@@ -334,8 +351,29 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
                                         if (CUT && old == SPOS_NONE) atomicAdd(&s_flags[2], 1);
                                     }
                                 }
+                                found[g] |= __shfl_sync(0xffffffffu, incl, 31);
                             }
-                            found[g] |= __reduce_or_sync(0xffffffffu, hit);
+                        } else {
+                            // every lane records its own new items (duplicates of one step
+                            // lose the atomicMin); cheaper where hits are sparse
+#pragma unroll
+                            for (int g = 0; g < G; ++g) {
+                                const uint32_t hit = raw[g] & ~found[g];
+                                if (hit) {
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        uint32_t m = word(w[u], 0x5504, g) & word(w[u], 0x5514, g) &
+                                                     word(w[u], 0x5524, g) & word(w[u], 0x5534, g) & hit;
+                                        while (m) {
+                                            const int b = __ffs(m) - 1;
+                                            m &= m - 1;
+                                            const uint32_t old = atomicMin(&s_best[g * 32 + b], pos0 + u);
+                                            if (CUT && old == SPOS_NONE) atomicAdd(&s_flags[2], 1);
+                                        }
+                                    }
+                                }
+                                found[g] |= __reduce_or_sync(0xffffffffu, hit);
+                            }
                         }
                     }
                 }
@@ -352,43 +390,32 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
     }
 }
 
+// Launch shape: as many blocks as are resident at once (the occupancy calculator: threads,
+// registers and shared memory), one wave of long blocks, so each block's set-up is paid
+// once; the sorted mode spreads its chunks (at least four stages each) over the nodes'
+// live ranges [0, cut), and the blocks past a node's cut leave at once.
 template <int G, bool CUT>
-static int sliced_variant(const SlicedArgs& A, dim3 grid, cudaStream_t s)
+static int sliced_launch(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc,
+                         uint32_t* list_best, int cap, int sets, uint32_t* status, cudaStream_t s)
 {
     static unsigned long long ctx[64] = {0};
-    if (first_in_context(ctx))
+    static int resident[64] = {0};
+    const int d = device_id();
+    if (first_in_context(ctx)) {
         BN_CUDA(cudaFuncSetAttribute(k_scan_sliced<G, CUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sl_smem(G)));
-    k_scan_sliced<G, CUT><<<grid, SL_THREADS, sl_smem(G), s>>>(A);
-    BN_LAUNCH_CHECK("k_scan_sliced");
-    return BN_OK;
-}
-
-bool sliced_supported(const bn_table* t) { return t->sset != nullptr; }
-
-int launch_scan_sliced(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc, uint32_t* list_best,
-                       int cap, bool cut, uint32_t* status, cudaStream_t s)
-{
-    if (!t->sset) return set_error(BN_EUNSUPPORTED, "sliced scan: needs k <= 4 (k = %d)", t->k);
-    if (cap < 1) return BN_OK;
-    const int per = std::min(cap, 256);
-    const int G = per <= 32 ? 1 : (per <= 64 ? 2 : (per <= 128 ? 4 : 8));
-    const int sets = (cap + 32 * G - 1) / (32 * G);
-    if (sets > 65535) return set_error(BN_EUNSUPPORTED, "sliced scan: %d items per node (at most %d)", cap, 65535 * 256);
-    // resident blocks per SM for this G (shared memory, 2,048 threads); one wave of long
-    // blocks, each block's set-up paid once (the sorted mode: at least four stages a
-    // block over the nodes' live ranges)
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>((size_t)(2048 / SL_THREADS),
-                                                                  (size_t)(224 * 1024) / (sl_smem_total(G) + 1024)));
+        int nb = 0;
+        BN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_sliced<G, CUT>, SL_THREADS, sl_smem(G)));
+        if (d >= 0 && d < 64) resident[d] = std::max(1, nb);
+    }
+    const int per_sm = (d >= 0 && d < 64 && resident[d] > 0) ? resident[d] : 1;
     const int64_t want = (int64_t)sm_count() * per_sm;
     int64_t chunk, nchunk;
-    if (!cut) {
+    if (!CUT) {
         nchunk = std::max<int64_t>(1, want / ((int64_t)t->n * sets));
         chunk = round_up((t->S + nchunk - 1) / nchunk, SL_SUB);
         nchunk = (t->S + chunk - 1) / chunk;
     } else {
-        // chunks over each node's live range [0, cut): about `want` blocks hold work, the
-        // blocks past a node's cut leave at once
         int64_t live = 0, longest = 0;
         for (int i = 0; i < t->n; ++i) {
             live += t->cut[i];
@@ -400,12 +427,30 @@ int launch_scan_sliced(const bn_table* t, const uint32_t* list_count, const uint
     SlicedArgs A{t->sset, t->spos, t->Sp, t->S, t->sset_stride, t->n, chunk, (int)nchunk, list_count, list_pc,
                  list_best, cap, status};
     dim3 grid((unsigned)(nchunk * t->n), (unsigned)sets);
+    k_scan_sliced<G, CUT><<<grid, SL_THREADS, sl_smem(G), s>>>(A);
+    BN_LAUNCH_CHECK("k_scan_sliced");
+    return BN_OK;
+}
+
+int launch_scan_sliced(const bn_table* t, const uint32_t* list_count, const uint64_t* list_pc, uint32_t* list_best,
+                       int cap, bool cut, uint32_t* status, cudaStream_t s)
+{
+    if (!t->sset) return set_error(BN_EUNSUPPORTED, "sliced scan: needs k <= 4 (k = %d)", t->k);
+    if (cap < 1) return BN_OK;
+    const int per = std::min(cap, 256);
+    const int G = per <= 32 ? 1 : (per <= 64 ? 2 : (per <= 128 ? 4 : 8));
+    const int sets = (cap + 32 * G - 1) / (32 * G);
+    if (sets > 65535) return set_error(BN_EUNSUPPORTED, "sliced scan: %d items per node (at most %d)", cap, 65535 * 256);
+#define BN_SL(GG)                                                                                               \
+    return cut ? sliced_launch<GG, true>(t, list_count, list_pc, list_best, cap, sets, status, s)               \
+               : sliced_launch<GG, false>(t, list_count, list_pc, list_best, cap, sets, status, s)
     switch (G) {
-        case 1: return cut ? sliced_variant<1, true>(A, grid, s) : sliced_variant<1, false>(A, grid, s);
-        case 2: return cut ? sliced_variant<2, true>(A, grid, s) : sliced_variant<2, false>(A, grid, s);
-        case 4: return cut ? sliced_variant<4, true>(A, grid, s) : sliced_variant<4, false>(A, grid, s);
-        default: return cut ? sliced_variant<8, true>(A, grid, s) : sliced_variant<8, false>(A, grid, s);
+        case 1: BN_SL(1);
+        case 2: BN_SL(2);
+        case 4: BN_SL(4);
+        default: BN_SL(8);
     }
+#undef BN_SL
 }
 
 }  // namespace bn
