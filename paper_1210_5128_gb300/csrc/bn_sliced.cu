@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
     // one record per item and step (measured: faster everywhere but in the full pass over
     // eight groups, where hits are sparse and the prefix ORs cost more than the duplicates)
     constexpr bool DEDUP = CUT || G <= 4;
+    // positions traded with the node's other chunks after each refill (measured: faster
+    // but for the full pass over eight groups, whose short, load-bound stages the trade's
+    // global round trip would hold back)
+    constexpr bool TRADE = CUT || G <= 4;
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t* s_ent = (uint32_t*)smem;                                            // [STAGES][SUB]
     // P[v][g] for lane l at word (g / 2) * ROWS * 64 + v * 64 + (g % 2) * 32 + l: a row of
@@ -202,6 +206,8 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
                 if (lane == 0) s_skip[g] = d;
                 pre += __popc(d);
             }
+        } else if (lane < G) {
+            s_skip[lane] = 0;
         }
         if (lane == 0) {
             s_flags[0] = 0;                                                       // abort
@@ -236,7 +242,8 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
     __syncthreads();
     if (CUT && s_flags[2] == nvalid) return;                                      // block-uniform; nothing issued
 
-    if (producer) {
+    if (producer && !TRADE) {
+        // lane 0 alone refills each stage once every consumer has released it
         if (lane == 0) {
             int issued = min(SL_STAGES, nsub);
             for (int it = 0; it + SL_STAGES < nsub; ++it) {
@@ -247,17 +254,75 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
                     atomicOr(A.status, STATUS_TIMEOUT);
                     break;
                 }
-                if (CUT && *(volatile int*)&s_flags[2] >= nvalid) {
+                issue(it + SL_STAGES, st);
+                issued = it + SL_STAGES + 1;
+            }
+            // no copy may still be in flight when the block's shared memory goes away
+            for (int j = max(0, issued - SL_STAGES); j < issued; ++j)
+                mbar_wait_bounded(&bar[j % SL_STAGES], (uint32_t)((j / SL_STAGES) & 1), WAIT_TIMEOUT_NS);
+        }
+    } else if (producer) {
+        // Lane 0 refills each stage once every consumer has released it.  Then, while the
+        // copy is in flight, the whole warp trades positions with the blocks of the node's
+        // other chunks: it publishes this block's new positions (atomicMin) and marks as
+        // skipped every item that already holds a position above this chunk -- no entry
+        // of the chunk can win for it, so the consumers stop testing it (they still read
+        // every entry).
+        int issued = min(SL_STAGES, nsub);
+        uint32_t pub[G], known[G];         // last published position; items already skipped
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            pub[g] = SPOS_NONE;
+            known[g] = s_skip[g];          // (the sorted mode's items skipped at the start are
+        }                                  // counted already)
+        for (int it = 0; it + SL_STAGES < nsub; ++it) {
+            const int st = it % SL_STAGES;
+            int go = 1;
+            if (lane == 0) {
+                if (*(volatile int*)&s_flags[0]) {
+                    go = 0;
+                } else if (!mbar_wait_bounded(&ebar[st], (uint32_t)((it / SL_STAGES) & 1), WAIT_TIMEOUT_NS)) {
+                    *(volatile int*)&s_flags[0] = 1;
+                    atomicOr(A.status, STATUS_TIMEOUT);
+                    go = 0;
+                } else if (CUT && *(volatile int*)&s_flags[2] >= nvalid) {
                     // every item holds a position: no unread entry can win; release the
                     // consumers of this buffer's next phase without a copy
                     *(volatile int*)&s_flags[1] = it + SL_STAGES;
                     mbar_arrive(&bar[st]);
                     issued = it + SL_STAGES + 1;
-                    break;
+                    go = 0;
+                } else {
+                    issue(it + SL_STAGES, st);
+                    issued = it + SL_STAGES + 1;
                 }
-                issue(it + SL_STAGES, st);
-                issued = it + SL_STAGES + 1;
             }
+            if (!__shfl_sync(0xffffffffu, go, 0)) break;
+            // every load first (one round trip for all groups), then the updates
+            uint32_t mine[G], other[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int item = g0 + 32 * g + lane;
+                const bool live = item < cnt && !((known[g] >> lane) & 1u);
+                mine[g] = live ? *(volatile const uint32_t*)&s_best[g * 32 + lane] : SPOS_NONE;
+                other[g] = live ? *(volatile const uint32_t*)&A.list_best[(size_t)node * A.cap + item] : SPOS_NONE;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int item = g0 + 32 * g + lane;
+                if (mine[g] < pub[g] && mine[g] < other[g]) {
+                    atomicMin(&A.list_best[(size_t)node * A.cap + item], mine[g]);
+                    pub[g] = mine[g];
+                }
+                const bool sk = other[g] < (uint32_t)e0;
+                // in the sorted mode the item now holds a position (for the stop)
+                if (CUT && sk && atomicMin(&s_best[g * 32 + lane], other[g]) == SPOS_NONE) atomicAdd(&s_flags[2], 1);
+                const uint32_t bits = __ballot_sync(0xffffffffu, sk);
+                known[g] |= bits;
+                if (lane == 0 && bits) *(volatile uint32_t*)&s_skip[g] |= bits;
+            }
+        }
+        if (lane == 0) {
             // no copy may still be in flight when the block's shared memory goes away
             for (int j = max(0, issued - SL_STAGES); j < issued; ++j)
                 mbar_wait_bounded(&bar[j % SL_STAGES], (uint32_t)((j / SL_STAGES) & 1), WAIT_TIMEOUT_NS);
@@ -268,7 +333,7 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
         for (int g = 0; g < G; ++g) {
             const int nv = min(max(cnt - g0 - 32 * g, 0), 32);
             found[g] = nv >= 32 ? 0u : (0xffffffffu << nv);
-            if (CUT) found[g] |= s_skip[g];
+            found[g] |= s_skip[g];
         }
         const uint32_t lane4 = (uint32_t)lane * 4u;
         const uint8_t* Pb = (const uint8_t*)s_P;
@@ -289,6 +354,7 @@ __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
             uint32_t all_found = 0xffffffffu;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
+                if constexpr (TRADE) found[g] |= *(volatile const uint32_t*)&s_skip[g];
                 all_found &= found[g];
             }
             if (all_found != 0xffffffffu) {
