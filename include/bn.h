@@ -322,7 +322,7 @@ int bn_chains_read(const bn_chains* c, int what, void* out, int mem, void* strea
 
 void bn_chains_free(bn_chains* c);
 
-/* Summary of a bn_mcmc_run (the edge-posterior ESS of the benchmark spec's metric):
+/* Summary of a bn_mcmc_run (the sampler's acceptance and edge-posterior ESS):
  * acceptance over the sampling steps; per directed edge m -> i the Geyer initial-
  * monotone-sequence ESS of its indicator series (every thin-th post-burn-in state),
  * summed over the chains in which the series is not constant; median and minimum over
