@@ -219,7 +219,8 @@ FUSED_INST_PER_CHAIN_STEP = 789.0
 FUSED_TRAFFIC_BYTES = 2.142e6    # ncu dram bytes read + written per 1,000-step launch of k_chain_spec<1>
 BUILD_INST_PER_ENTRY = 649.0     # ncu smsp__inst_executed.sum of k_build<4,1,0> per entry at n=60, m=1000
 SCAN_TRAFFIC_BYTES = 121.5e6
-SLICED_TRAFFIC_BYTES = 120.44e6  # ncu dram bytes read + written per launch of k_scan_sliced<1,0> at 32 orders
+NODES_TRAFFIC_BYTES = 124.2e6    # ncu dram bytes read + written per launch of k_scan_nodes at one order
+SLICED_TRAFFIC_BYTES = 120.37e6  # ncu dram bytes read + written per launch of k_scan_sliced<1,0> at 32 orders
 
 
 def _flush_l2(torch, flush, stream):
@@ -857,7 +858,8 @@ def main():
                                      "issue slots busy, DRAM below peak)"},
             "roofline_hbm_one_order": {"kernel": "k_scan_nodes (bn_score_orders, BN_SCAN_FULL, one order)",
                                        "bound": "hbm", "achieved": hbm_leg[0]["achieved_gbs"], "peak": hbm_peak,
-                                       "unit": "GB/s", "frac": hbm_leg[0]["frac"], "bytes_algorithmic": hbm_bytes},
+                                       "unit": "GB/s", "frac": hbm_leg[0]["frac"], "bytes_algorithmic": hbm_bytes,
+                                       "traffic": NODES_TRAFFIC_BYTES},
             "score_orders": {"by_orders": hbm_leg, "sliced": sliced_leg, "sorted": sorted_leg,
                              "test_rate_peak": test_rate, "pruned_table": pruned_scoring,
                              "note": "bn_score_orders on B random orders of the full n=60 table: scan kernel time "
