@@ -154,3 +154,35 @@ def test_sliced_modes_need_k_at_most_4(gpu):
     for b, o in enumerate(orders):
         s_ref, r_ref = oracle.order_score(tab, 5, o)
         assert np.array_equal(br[b], r_ref) and sc[b] == s_ref
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,k,B", [(2, 1, 5), (3, 0, 7), (64, 2, 70), (64, 3, 33)])
+def test_smallest_and_largest_networks(gpu, mode, n, k, B):
+    """Edge sizes of the byte-per-parent layout: two nodes, no parents at all (k = 0, the
+    empty set only), and 64 nodes, whose ids run up to 63 next to the "no parent" and
+    "never" rows (64, 65); seeded random tables with exact ties."""
+    rng = np.random.default_rng(n * 100 + k)
+    S = oracle.num_sets(n - 1, k)
+    tab = rng.integers(-40, 1, size=(n, S)).astype(np.float64) / 4.0
+    _check_shared(gpu, tab, k, synth.random_orders(n, B, 7 + n), mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_oracle_built_n60_table(gpu, oracle_n60, mode):
+    """The oracle's own n = 60 table (29.4 M entries, built on the host) scored on the GPU
+    in the bench's batch shape: every order's ranks and FP64 sum equal the mask-test
+    scan's, and a sample equals the oracle's own order scores."""
+    data, arity, k, R, tab = oracle_n60
+    n = data.shape[1]
+    t = gpu.table_from_scores(tab, k)
+    orders = synth.random_orders(n, 97, 61)
+    br0, sc0 = gpu.score_orders(t, orders)
+    gpu.table_set_scan(t, _mode(gpu, mode))
+    br, sc = gpu.score_orders(t, orders)
+    assert np.array_equal(br, br0) and np.array_equal(sc, sc0)
+    for b in (0, 31, 32, 96):
+        s_ref, r_ref = oracle.order_score(tab, k, orders[b])
+        assert np.array_equal(br[b], r_ref)
+        assert sc[b] == s_ref
+    t.free()
