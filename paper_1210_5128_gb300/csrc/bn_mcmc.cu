@@ -917,6 +917,7 @@ __global__ void __launch_bounds__(32 * BATCH_WARPS) k_batch_fused(const ChainSta
 // ---------------------------------------------------------------------------------
 static constexpr int SPEC_WARPS = 4;       // warps per chain
 static constexpr int SPEC_BATCH = 64;      // Philox draws prepared at a time
+static constexpr int SPEC_PROBE = 8;      // survivors each lane tests of its own walks first
 
 struct SpecBatch {                         // steps base .. base + SPEC_BATCH - 1
     uint8_t ra[SPEC_BATCH], rb[SPEC_BATCH];
@@ -1102,10 +1103,31 @@ __device__ __forceinline__ void chain_spec_body(const ChainState& S, const Fused
                     act[h] = !(none_before && stays);
                 }
             }
+            // each lane first tests the first SPEC_PROBE survivors of its own walks, all loads
+            // independent: a walk whose answer lies there is done without the warp-wide
+            // walk (the same answer: the first consistent survivor in index order); the
+            // others go on from the first survivor not probed
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!act[h]) continue;
+                uint64_t pm[SPEC_PROBE];
+#pragma unroll
+                for (int r = 0; r < SPEC_PROBE; ++r) pm[r] = wj[h] + r < wj1[h] ? c_mask[wj[h] + r] : ~0ull;
+                int first = SPEC_PROBE;
+#pragma unroll
+                for (int r = SPEC_PROBE - 1; r >= 0; --r)
+                    if ((pm[r] & wnpc[h]) == 0ull) first = r;
+                if (first < SPEC_PROBE) {
+                    wj[h] += first;
+                    act[h] = false;
+                } else {
+                    wj[h] += SPEC_PROBE;
+                }
+            }
         }
-        // the round's re-scoring walks (the nodes that cannot keep their parent sets, ~3 a
-        // step) are shared by the four warps, so a step with many of them does not hold the
-        // round back: each warp posts its own, all walk them in turn, each takes its answers
+        // the round's remaining re-scoring walks are shared by the four warps, so a step with
+        // many of them does not hold the round back: each warp posts its own, all walk them
+        // in turn, each takes its answers
         int ti[2] = {0, 0};
         {
             const unsigned m0 = __ballot_sync(0xffffffffu, act[0]), m1 = __ballot_sync(0xffffffffu, act[1]);
