@@ -215,8 +215,8 @@ ISSUE_PER_SM = 4           # warp schedulers per SM, one warp instruction per cl
 # launches; all four warps of a chain, the dropped speculative evaluations included), per
 # chain per committed MH iteration; and dram__bytes_read.sum + dram__bytes_write.sum per
 # launch of the full-table k_scan<1024,0> (256 items per node, the sampler's step)
-FUSED_INST_PER_CHAIN_STEP = 789.0
-FUSED_TRAFFIC_BYTES = 2.142e6    # ncu dram bytes read + written per 1,000-step launch of k_chain_spec<1>
+FUSED_INST_PER_CHAIN_STEP = 760.0
+FUSED_TRAFFIC_BYTES = 2.146e6    # ncu dram bytes read + written per 1,000-step launch of k_chain_spec<1>
 BUILD_INST_PER_ENTRY = 649.0     # ncu smsp__inst_executed.sum of k_build<4,1,0> per entry at n=60, m=1000
 SCAN_TRAFFIC_BYTES = 121.5e6
 NODES_TRAFFIC_BYTES = 124.2e6    # ncu dram bytes read + written per launch of k_scan_nodes at one order
