@@ -105,6 +105,7 @@ __device__ __forceinline__ uint32_t warp_walk(const uint64_t* m, uint32_t js, ui
 // with warp walks always against 1.70 us with lane walks above 8 nodes and 1.73 us above
 // 3); with more, every lane first walks its own nodes for 16 survivors and the warp then
 // walks those still open (every span node re-scored: uncached networks, learned steps).
+constexpr int WALK_PROBE = 8;   // survivors each lane tests of its own nodes before the warp walks
 __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], const uint32_t (&j1)[2],
                                           const uint64_t (&npc)[2], const bool (&act)[2], int lane,
                                           int warp_max)
@@ -112,9 +113,30 @@ __device__ __forceinline__ void span_walk(const uint64_t* m, uint32_t (&j)[2], c
     {
         const unsigned p0 = __ballot_sync(0xffffffffu, act[0]), p1 = __ballot_sync(0xffffffffu, act[1]);
         if (__popc(p0) + __popc(p1) <= warp_max) {
+            // each lane first tests the first WALK_PROBE survivors of its own nodes, all loads
+            // independent; a node whose answer lies there needs no warp walk (the same answer:
+            // the first qualifying survivor in index order), the others go on after them
+            bool open[2] = {act[0], act[1]};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                unsigned pend = h ? p1 : p0;
+                if (!open[h]) continue;
+                uint64_t pm[WALK_PROBE];
+#pragma unroll
+                for (int r = 0; r < WALK_PROBE; ++r) pm[r] = j[h] + r < j1[h] ? m[j[h] + r] : ~0ull;
+                int first = WALK_PROBE;
+#pragma unroll
+                for (int r = WALK_PROBE - 1; r >= 0; --r)
+                    if ((pm[r] & npc[h]) == 0ull) first = r;
+                if (first < WALK_PROBE) {
+                    j[h] += first;
+                    open[h] = false;
+                } else {
+                    j[h] += WALK_PROBE;
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned pend = __ballot_sync(0xffffffffu, open[h]);
                 while (pend) {
                     const int src = __ffs(pend) - 1;
                     pend &= pend - 1;
