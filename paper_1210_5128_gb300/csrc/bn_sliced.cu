@@ -8,10 +8,11 @@
 // An entry with parent nodes {v1, .., vj} (j <= k <= 4) is consistent with exactly the
 // items of P[v1][g] & .. & P[vj][g]: four shared-memory words and three ANDs test one
 // entry against 32 orders at once.  Of those items, the ones this warp has not found
-// yet take the entry's sorted position (a shared-memory atomicMin, once per item and
-// warp, plus the few duplicates of one 32-entry step), and a warp-wide OR marks them
-// found.  Every later entry of the warp lies further down the sorted list, so it can
-// only lose.
+// yet take the entry's sorted position (a shared-memory atomicMin, by the lowest lane of
+// a step that hits the item), and a warp-wide OR marks them found.  Every later entry of
+// the warp lies further down the sorted list, so it can only lose.  Blocks of the same
+// node also trade positions across chunks through the work list: an item that already
+// holds a position above a block's chunk is not tested there at all.
 //
 // The entries reach shared memory as one 4-byte word each (the parent node ids, a byte
 // apiece, in sorted-position order; `sset`), streamed by 1-D bulk (TMA) copies, so a
@@ -26,7 +27,6 @@
 // entry still unread lies further down the list), and a block whose items all hold a
 // position above its chunk already (from blocks of earlier chunks) does nothing.
 #include <algorithm>
-#include <mutex>
 
 #include "bn_table.cuh"
 
@@ -130,18 +130,18 @@ int build_sset(bn_table* t, cudaStream_t s)
     return BN_OK;
 }
 
-// Block (chunk c, node i) = blockIdx.x = c * n + i, item set blockIdx.y: items
-// 32 G y .. 32 G y + 32 G - 1 of node i.  Eight consumer warps and one producer warp:
-// consumer warp w tests entries w * 256 .. w * 256 + 255 of every stage, 32 a step, so
-// each warp walks its entries in increasing sorted position; the producer refills a stage
-// as soon as every consumer has released it (an empty mbarrier per stage), so no
-// consumer waits for a refill.
 // word index of P[v][g] for lane 0
 __device__ __forceinline__ int Pw(int g, int v)
 {
     return (g >> 1) * SL_ROWS * (SL_ROW_BYTES / 4) + v * (SL_ROW_BYTES / 4) + (g & 1) * 32;
 }
 
+// Block (chunk c, node i) = blockIdx.x = c * n + i, item set blockIdx.y: items
+// 32 G y .. 32 G y + 32 G - 1 of node i.  Eight consumer warps and one producer warp:
+// consumer warp w tests entries w * 256 .. w * 256 + 255 of every stage, 128 a step, so
+// each warp walks its entries in increasing sorted position; the producer refills a stage
+// as soon as every consumer has released it (an empty mbarrier per stage), so no
+// consumer waits for a refill.
 template <int G, bool CUT>
 __global__ void __launch_bounds__(SL_THREADS) k_scan_sliced(SlicedArgs A)
 {
