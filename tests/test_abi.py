@@ -116,3 +116,27 @@ def test_argument_checks_of_batch_and_run_calls(bn):
     assert L.bn_mcmc_run(None, C.byref(p), 10, None, None, None, None, None, None) == bn.EINVAL
     assert L.bn_chains_set_learned_launch(None, 0) == bn.EINVAL
     assert L.bn_measure_test_rate(None, None) == bn.EINVAL
+
+
+def test_binding_constants_equal_the_header(bn):
+    """Every named constant the Python binding passes through the C ABI (error codes,
+    memory kinds, scan modes, output ids, proposal kinds, learned launch modes) has the
+    value bn.h defines, so a call never sends one mode meaning another."""
+    src = open(os.path.join(ROOT, "include", "bn.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define BN_([A-Z0-9_]+)\s+(-?\d+)", src, flags=re.M)}
+    checked = 0
+    for name, value in defs.items():
+        if name.startswith("OUT_"):
+            assert bn.OUT[name[4:].lower()] == value, name
+        elif name.startswith("MLP_"):
+            continue                               # tensor ids: bn.MLP_TENSORS order, below
+        elif hasattr(bn, name):
+            assert getattr(bn, name) == value, name
+        else:
+            continue
+        checked += 1
+    assert checked >= 30
+    for i, t in enumerate(bn.MLP_TENSORS):
+        assert defs["MLP_" + t.upper()] == i
+    for mode in ("FULL", "PRUNED", "UNRANK", "SLICED", "SORTED"):
+        assert getattr(bn, "SCAN_" + mode) == defs["SCAN_" + mode]
