@@ -11,7 +11,8 @@ parent sets per node, 29.36 M FP64 entries, 235 MB), 256 chains.
 The headline runs the pruned table (only entries that no subset of their parent set
 matches or beats -- the same results, see include/bn.h) in the fused sampler, one launch
 per timed step; the full-table scan (three kernels per iteration, replayed from a CUDA
-graph) is timed beside it with its own roofline.  Edge-posterior ESS/s of the plain uniform-swap
+graph) is timed beside it with its own roofline, in the mask-test and the two bit-sliced
+scan modes, and bn_score_orders is swept over batch sizes in each mode.  Edge-posterior ESS/s of the plain uniform-swap
 sampler and of the learned-proposal sampler (trained on the plain sampler's history) are
 measured on the same table.
 
